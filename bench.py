@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the PLAS grid sort on GB300 (one JSON line on rank 0).
+
+Metric: milliseconds per 1M x 14-D grid sort -- one complete sort of a
+1024 x 1024 grid (N = 1,048,576) of 14 sort channels with 45 carried
+channels, 3DGS-shaped synthetic data, default schedule, inputs resident in HBM.
+A step is one full call of plas_sort (normalise, initial placement, every
+iteration of the shrinking-radius schedule, permutation + carried gather).
+
+  python bench.py [--steps K] [--warmup W] [--workload m1|cfg2|cfg3|cfg1|p0]
+  python bench.py --impl reference      # the CPU oracle on this host's cores
+
+Under torchrun (N > 1) every rank sorts its own replica (different seed): the
+sort has no data-path exchange, so the job is N independent replicas and
+'value' is the whole-job time per sort (max-over-ranks elapsed / sorts done).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "m1": dict(side=1024, D=14, C=45, kind="3dgs",
+               desc="1024x1024 grid (N=1,048,576), 14 sort + 45 carried fp32 channels, "
+                    "3DGS-shaped synthetic attributes, seed 0, default schedule"),
+    "cfg2": dict(side=512, D=14, C=45, kind="3dgs",
+                 desc="512x512 grid (N=262,144), 14 sort + 45 carried fp32, 3DGS-shaped"),
+    "cfg3": dict(side=1448, D=14, C=45, kind="3dgs",
+                 desc="1448x1448 grid (N=2,096,704), 14 sort + 45 carried fp32, 3DGS-shaped"),
+    "cfg1": dict(side=64, D=3, C=0, kind="rgb",
+                 desc="64x64 grid (N=4096), 3 fp32 channels U[0,1)"),
+    "p0": dict(side=512, D=3, C=0, kind="rgb",
+               desc="512x512 grid (N=262,144), 3 fp32 channels U[0,1) (paper's runtime test)"),
+}
+METRIC = "ms per 1M x 14-D grid sort"
+FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
+
+# Per-launch DRAM traffic of the dominant kernels from committed ncu
+# summaries (profiles/), keyed by the sha1 of the kernel source they were
+# taken on; a stale hash reports null.
+NCU_TRAFFIC = {}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2312_13299_gb300", "csrc", "sort_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="plas_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [t.strip() for t in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows]
+        util = [num(r[4]) for r in rows]
+        loaded = [s for s, u in zip(sm, util) if s is not None and u is not None and u >= 50]
+        if not loaded:
+            loaded = [s for s in sm if s is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(wl, seed=0):
+    from paper_2312_13299_gb300 import synth
+    n = wl["side"] * wl["side"]
+    if wl["kind"] == "rgb":
+        return synth.rgb_uniform(wl["side"], seed=seed), None
+    return synth.gaussians_3dgs(n, seed=seed, with_carried=wl["C"] > 0)
+
+
+def pass_fmas(length, r, other, D):
+    t = 0
+    for p in range(length):
+        t += min(r, length - 1 - p) - max(-r, -p) + 1
+    return t * other * D
+
+
+def roofline(stats_list, peaks, peaks_src, clocks, wl):
+    """Dominant kernel class of the timed steps and its achieved rate."""
+    agg = {}
+    for st in stats_list:
+        for name, k in st["kernels"].items():
+            a = agg.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for f in a:
+                a[f] += k[f]
+    name = max(agg, key=lambda n: agg[n]["ms"])
+    k = agg[name]
+    total_ms = sum(a["ms"] for a in agg.values()) or 1.0
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * FP32_FMA_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm = peaks["hbm_gbs"]
+    secs = k["ms"] / 1e3
+    gbs = k["bytes"] / secs / 1e9 if secs > 0 else 0.0
+    tfl = k["flops"] / secs / 1e12 if secs > 0 else 0.0
+    if k["flops"] > 0 and tfl / fp32_peak_tflops > gbs / hbm:
+        out = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp32_peak_tflops, 2),
+               "unit": "TFLOP/s", "frac": round(tfl / fp32_peak_tflops, 4),
+               "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz"}
+    else:
+        out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+               "frac": round(gbs / hbm, 4), "peak_source": f"{peaks_src} hbm_gbs"}
+    tr = NCU_TRAFFIC.get((name, wl))
+    out.update({"kernel": name, "traffic": (tr["bytes_per_launch"] if tr and tr["src"] == _kernel_hash() else None),
+                "launches": int(k["launches"]), "avg_launch_us": round(k["ms"] * 1e3 / max(1, k["launches"]), 2),
+                "share": round(k["ms"] / total_ms, 4)})
+    per_kernel = {}
+    for n, a in agg.items():
+        s = a["ms"] / 1e3
+        per_kernel[n] = {"launches": int(a["launches"]), "ms": round(a["ms"], 3),
+                         "share": round(a["ms"] / total_ms, 4),
+                         "GB/s": round(a["bytes"] / s / 1e9, 1) if s > 0 else None,
+                         "TFLOP/s": round(a["flops"] / s / 1e12, 3) if s > 0 and a["flops"] else None}
+    return out, per_kernel
+
+
+def oracle_projection(x, wl, seed, level_counts, plas, max_cpu_s=30.0):
+    """Bounded CPU-oracle sample -> projected ms for the whole sort.
+
+    The oracle runs one and two iterations resumed from GPU snapshots at the
+    first iteration of a few sampled levels (the trajectories are identical,
+    as the parity tests show); the per-iteration cost at each sampled level
+    (two-iteration minus one-iteration wall time) is fitted as a + b*FMAs and
+    multiplied out over the per-level iteration counts of the schedule."""
+    import numpy as np
+    import torch
+    import oracle
+    side, D = wl["side"], wl["D"]
+    phis = oracle.levels(side, side)
+    first_it = np.concatenate([[0], np.cumsum(level_counts)[:-1]])
+    targets = [phis[0], 100.0, 10.0, 1.0]
+    sample_levels = sorted({int(np.argmin(np.abs(phis - t))) for t in targets})
+    xc = torch.from_numpy(x).cuda()
+    pts = []
+    t_start = time.time()
+    for L in sample_levels:
+        start = int(first_it[L])
+        snap = plas.sort(xc, side, side, seed=seed, schedule=plas.Schedule(max_iters=start))
+        perm0 = snap.perm.cpu().numpy()
+        st = oracle.State()
+        for kk, v in snap.state.items():
+            if hasattr(st, kk):
+                setattr(st, kk, v)
+        times = []
+        for n_it in (1, 2):
+            t0 = time.perf_counter()
+            oracle.sort(x, side, side, seed=seed, sched=oracle.default_schedule(max_iters=start + n_it),
+                        perm_in=perm0, state=st, trace_cap=1)
+            times.append(time.perf_counter() - t0)
+        r = int(math.floor(phis[L]))
+        fm = pass_fmas(side, min(r, side - 1), side, D) * 2
+        pts.append((fm, max(times[1] - times[0], 1e-6), L))
+        if time.time() - t_start > max_cpu_s:
+            break
+    A = np.array([[1.0, p[0]] for p in pts])
+    y = np.array([p[1] for p in pts])
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    a, b = float(max(coef[0], 0.0)), float(max(coef[1], 0.0))
+    total = 0.0
+    for L, n in enumerate(level_counts):
+        r = int(math.floor(phis[L]))
+        total += n * (a + b * pass_fmas(side, min(r, side - 1), side, D) * 2)
+    sample = (f"one and two oracle iterations resumed from snapshots at levels {[p[2] for p in pts]} "
+              f"(radii {[int(phis[p[2]]) for p in pts]}); per-iteration cost fitted as a + b*FMAs and "
+              f"projected over the schedule's {int(sum(level_counts))} iterations")
+    return total * 1e3, sample, time.time() - t_start
+
+
+def _dist_setup():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def _max_over_ranks(v, pg, device):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def run_plas(args):
+    import numpy as np
+    import torch
+    import paper_2312_13299_gb300 as plas
+    from paper_2312_13299_gb300 import build as _b
+    world, rank, local, pg = _dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not _b.up_to_date():
+        _b.build()
+    plas.load()
+    wl = WORKLOADS[args.workload]
+    side, D, C = wl["side"], wl["D"], wl["C"]
+    seed = rank
+    x_np, car_np = make_inputs(wl, seed=seed)
+    x = torch.from_numpy(x_np).to(dev)
+    car = torch.from_numpy(car_np).to(dev) if car_np is not None else None
+    ws = torch.empty(plas.sort_workspace_bytes(side, side, D), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(profile):
+        return plas.sort(x, side, side, carried=car, seed=seed, workspace=ws,
+                         schedule=plas.Schedule(profile=profile), want_stats=True)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    _barrier(pg)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    _barrier(pg)
+    e0.record(stream)
+    stats = [step(True).stats for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(pg)
+    elapsed_ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    max_ms = _max_over_ranks(elapsed_ms, pg, dev)
+    ms_per_sort = max_ms / (args.steps * world)
+    launches = int(sum(st["launches"] for st in stats))
+
+    # end to end: pinned host inputs in, permutation + carried out, per step
+    xh = torch.from_numpy(x_np).pin_memory()
+    ch = torch.from_numpy(car_np).pin_memory() if car_np is not None else None
+    ph = torch.empty(side * side, dtype=torch.int32).pin_memory()
+    coh = torch.empty_like(ch).pin_memory() if ch is not None else None
+    xd = torch.empty_like(x)
+    cd = torch.empty_like(car) if car is not None else None
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    _barrier(pg)
+    e2.record(stream)
+    for _ in range(n_e2e):
+        xd.copy_(xh, non_blocking=True)
+        if cd is not None:
+            cd.copy_(ch, non_blocking=True)
+        r = plas.sort(xd, side, side, carried=cd, seed=seed, workspace=ws)
+        ph.copy_(r.perm, non_blocking=True)
+        if coh is not None:
+            coh.copy_(r.carried, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _max_over_ranks(e2.elapsed_time(e3), pg, dev) / (n_e2e * world)
+    h2d = x_np.nbytes + (car_np.nbytes if car_np is not None else 0)
+    d2h = ph.numel() * 4 + (coh.numel() * 4 if coh is not None else 0)
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    peaks, psrc = _peaks()
+    rl, per_kernel = roofline(stats, peaks, psrc, ck, args.workload)
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": round(ms_per_sort, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded numpy; 3DGS-shaped attributes, no dataset)",
+        "config": {"workload": wl["desc"], "grid": f"{side}x{side}", "N": side * side, "D": D,
+                   "carried": C, "iterations_per_sort": st0["iterations"], "levels": st0["levels"],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush"},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "roofline": rl,
+        "kernels": per_kernel,
+        "melem_iter_per_s": round(side * side * st0["iterations"] / (ms_per_sort / 1e3) / 1e6, 1),
+        "clocks": ck,
+    }
+    if args.cpu_baseline and world == 1:
+        counts = None
+        try:
+            tr = plas.sort(x, side, side, carried=None, seed=seed, trace_cap=1 << 18)
+            counts = np.bincount(tr.trace_level.cpu().numpy(), minlength=st0["levels"])
+            import oracle
+            proj_ms, sample, cpu_s = oracle_projection(x_np, wl, seed, counts, plas)
+            line["cpu_baseline"] = {"value": round(proj_ms, 1), "unit": "ms", "cores": oracle.num_threads(),
+                                    "kind": "oracle", "sample": sample, "cpu_seconds": round(cpu_s, 1),
+                                    "projected": True}
+        except Exception as e:  # reported, never silently replaced
+            line["cpu_baseline"] = {"value": None, "error": repr(e)}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, timed on this host's cores (rank 0 only)."""
+    import numpy as np
+    world, rank, local, pg = _dist_setup()
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    import torch
+    import oracle
+    import paper_2312_13299_gb300 as plas
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    side = wl["side"]
+    x_np, _ = make_inputs(wl, seed=0)
+    torch.cuda.set_device(local)
+    plas.load()
+    x = torch.from_numpy(x_np).cuda()
+    tr = plas.sort(x, side, side, seed=0, trace_cap=1 << 18)
+    counts = np.bincount(tr.trace_level.cpu().numpy(), minlength=len(oracle.levels(side, side)))
+    vals = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        v, sample, _ = oracle_projection(x_np, wl, 0, counts, plas, max_cpu_s=20.0)
+        if i >= args.warmup:
+            vals.append(v)
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded numpy; 3DGS-shaped attributes, no dataset)",
+            "config": {"workload": wl["desc"]},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="plas", choices=["plas", "reference"])
+    ap.add_argument("--workload", default="m1", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_plas(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,307 @@
+/*
+ * plas.h -- C ABI of the GB300 (sm_103a) implementation of Parallel Linear
+ * Assignment Sorting (PLAS) and of the grid smoothness loss from
+ * Morgenstern et al., "Compact 3D Scene Representation via Self-Organizing
+ * Gaussian Grids" (arXiv 2312.13299).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers marked "device" are CUDA device (or managed) pointers; "host"
+ *    pointers are ordinary CPU memory.  The caller owns every buffer passed
+ *    in; the library never frees or retains caller memory after a call.
+ *  - Grids are row-major: cell (y, x) of an H x W grid is row y*W + x of an
+ *    N x K matrix (N = H*W, K values per cell, contiguous).  All floating
+ *    point data is IEEE float32.
+ *  - 'stream' is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work is enqueued on it, in order.
+ *  - Every function returns PLAS_OK (0) or a negative PLAS_ERR_* code; no
+ *    C++ exception crosses this boundary.  plas_last_error() gives a
+ *    human-readable message for the most recent failure on the calling
+ *    thread.  Invalid arguments are rejected before any work is enqueued.
+ *  - Results are a pure function of the inputs, the seed and the schedule:
+ *    no floating-point reduction whose order depends on scheduling feeds a
+ *    decision of the sort.
+ */
+#ifndef PLAS_H_
+#define PLAS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* status codes                                                           */
+/* ---------------------------------------------------------------------- */
+#define PLAS_OK 0
+#define PLAS_ERR_INVALID_ARG (-1) /* bad size, NULL pointer, misalignment   */
+#define PLAS_ERR_OOM (-2)         /* device allocation failed               */
+#define PLAS_ERR_CUDA (-3)        /* a CUDA runtime call failed             */
+#define PLAS_ERR_TIMEOUT (-4)     /* a bounded device wait gave up          */
+#define PLAS_ERR_NONFINITE (-5)   /* input holds NaN or +-Inf               */
+#define PLAS_ERR_BUDGET (-6)      /* batch does not fit its memory budget   */
+#define PLAS_ERR_INTERNAL (-7)    /* an internal consistency check failed   */
+
+/* ---------------------------------------------------------------------- */
+/* schedule of the sort (Sec. 3.1, "Sorting High Dimensional Gaussians")  */
+/* ---------------------------------------------------------------------- */
+typedef struct plas_schedule {
+    double phi0;        /* start radius; <= 0 selects min(H,W)/2 - 1, the    */
+                        /* paper's w/2 - 1 (Sec. 3.1)                        */
+    double shrink;      /* radius factor per level, 0.95 (Sec. 3.1)          */
+    double phi_min;     /* the sort ends when phi falls below this, 1.0      */
+    double tol;         /* relative improvement below which an assignment    */
+                        /* counts as a stall, 1e-4 (supplementary)           */
+    double sigma_ratio; /* Gaussian sigma = sigma_ratio * phi; the blur      */
+                        /* half-width is floor(phi) (paper silent on sigma)  */
+    int min_block;      /* smallest block side beta, 16 (Sec. 3.1)           */
+    int shuffle_init;   /* 1: random initial placement (Sec. 3.1); 0: start  */
+                        /* from the identity (or from perm_init)             */
+    int normalize;      /* 1: per-channel [0,1] normalisation before the     */
+                        /* weights (Sec. 3.1); 0: weights only               */
+    int iters_per_poll; /* iterations enqueued between two host reads of the */
+                        /* 64-byte device state; <= 0 selects 8              */
+    long long max_iters;/* stop once the iteration counter reaches this;     */
+                        /* 0 = run the full schedule                         */
+    int profile;        /* 1: time every kernel class with CUDA events and   */
+                        /* report it in plas_stats (adds event records)      */
+    int reserved;
+    long long* trace_S; /* device or NULL: trace_S[it] = fixed-point residual */
+                        /* sum of iteration it (mean L2 distance * N * 2^k)  */
+    int* trace_level;   /* device or NULL: level of iteration it             */
+    long long trace_cap;/* entries of the trace arrays                       */
+} plas_schedule;
+
+/* Resumable schedule state: together with the permutation it is a complete
+ * snapshot of a sort in progress (the random streams are counter-based). */
+typedef struct plas_state {
+    long long it;       /* iterations done                                   */
+    long long epoch;    /* block-shift epoch (a new random shift per epoch)  */
+    long long redraws;  /* shift redraws caused by a stall                   */
+    int level;          /* index of the current radius in the phi sequence   */
+    int stall;          /* 1 after one non-improving assignment              */
+    int has_prev;       /* d_prev valid (0 right after a level change)       */
+    int done;           /* 1 once the radius fell below phi_min              */
+    double d_prev;      /* mean L2 distance to the target, previous iteration */
+    double d_last;      /* mean L2 distance to the target, last iteration    */
+    int scale_exp;      /* exponent k of the fixed-point residual sum        */
+    int status;         /* device-side status word (PLAS_OK or an error)     */
+} plas_state;
+
+/* kernel classes reported by plas_stats.kernel[] */
+#define PLAS_K_PREP 0     /* min/max, normalise, initial placement           */
+#define PLAS_K_BLUR_ROWS 1/* target, pass along x                            */
+#define PLAS_K_BLUR_COLS 2/* target, pass along y                            */
+#define PLAS_K_GROUPS 3   /* grouping permutation of the block cells         */
+#define PLAS_K_ASSIGN 4   /* 24-permutation scoring, swap, residual, schedule */
+#define PLAS_K_GATHER 5   /* permutation + carried-attribute gather          */
+#define PLAS_K_COUNT 6
+
+typedef struct plas_kernel_stat {
+    long long launches; /* launches of this class (including no-op ones)     */
+    double ms;          /* summed CUDA-event time                            */
+    double bytes;       /* algorithmic bytes moved (see the design notes)    */
+    double flops;       /* algorithmic floating-point operations             */
+} plas_kernel_stat;
+
+typedef struct plas_stats {
+    long long iterations;   /* assignments performed                          */
+    long long redraws;      /* shift redraws                                  */
+    long long grouped_cells;/* cells that took part in a group, summed        */
+    int levels;             /* radius levels in the schedule                  */
+    int status;             /* PLAS_OK or the device status word              */
+    double final_l2_to_target; /* mean L2 grid-to-target distance, last iter  */
+    double neighbour_l2;    /* mean L2 distance of 4-neighbours, final grid   */
+    double ms_total;        /* wall time of the call (host clock)             */
+    long long launches;     /* kernel launches made by the call (idle ones    */
+                            /* after a level change included)                 */
+    plas_kernel_stat kernel[PLAS_K_COUNT]; /* filled when schedule.profile=1  */
+} plas_stats;
+
+/* Fill *out with the defaults above.  Returns PLAS_OK, or
+ * PLAS_ERR_INVALID_ARG if out is NULL. */
+int plas_default_schedule(plas_schedule* out);
+
+/* Number of radius levels the schedule runs for an H x W grid
+ * (phi_L = phi0 * shrink^L while phi_L >= phi_min).  Returns the count
+ * (>= 1) or a negative error code for invalid arguments. */
+int plas_num_levels(int H, int W, const plas_schedule* sched /* host or NULL */);
+
+/* Device workspace plas_sort needs for an H x W grid of D sort channels
+ * (C carried channels do not need workspace).  0 on invalid sizes. */
+size_t plas_sort_workspace_bytes(int H, int W, int D);
+
+/*
+ * plas_sort -- the PLAS grid sort (Sec. 3.1 and its "Blockwise Linear
+ * Assignment" and "Organizing Gaussians into a 2D Grid" paragraphs).
+ *
+ * Finds one permutation that places the N = H*W rows of x on an H x W grid
+ * so that grid neighbours are close in the weighted, normalised feature
+ * space; all attribute planes then follow that one permutation (Sec. 3,
+ * Fig. "grid2splat").
+ *
+ *   x            device, N x D float32: the sort features of each Gaussian
+ *                (activated values, Sec. 3.1).  1 <= D <= 64.
+ *   H, W         grid sides, H*W = N, 0 <= N <= 2^26.  N == 0 is a no-op.
+ *   weights      host, D floats (NULL = all ones): per-channel factors
+ *                applied after normalisation (Sec. 3.1, Tab. "params").
+ *   carried      device, N x C float32 or NULL: attributes that follow the
+ *                permutation (e.g. the 45 SH-rest coefficients).
+ *   C            carried channels (0 if carried is NULL).
+ *   seed         key of every random decision (initial placement, block
+ *                shifts, groupings); Philox4x32-10 counters, so results do
+ *                not depend on launch shapes or batch composition.
+ *   sched        host or NULL (defaults).
+ *   perm_init    device, N int32 or NULL: start arrangement (position p
+ *                holds Gaussian perm_init[p]).  Required when resuming.
+ *   state_io     host or NULL.  If non-NULL and state_io->it > 0 or
+ *                state_io->level > 0, the sort resumes from that state and
+ *                perm_init (a snapshot); on return it holds the final state.
+ *   perm_out     device, N int32: Gaussian index at each grid position
+ *                (gather form: sorted = x[perm_out]).
+ *   carried_out  device, N x C or NULL: carried[perm_out].
+ *   sorted_out   device, N x D or NULL: x[perm_out] (un-normalised).
+ *   workspace    device or NULL.  If non-NULL it must hold
+ *                plas_sort_workspace_bytes(H, W, D) bytes, 256-byte
+ *                aligned, and the call allocates nothing; if NULL the call
+ *                allocates and frees stream-ordered memory itself.
+ *   ws_bytes     size of workspace.
+ *   stats        host or NULL: filled after the sort (the call then waits
+ *                for the stream).
+ *   stream       cudaStream_t.
+ *
+ * The call reads a 64-byte state block back to the host every
+ * sched->iters_per_poll iterations, so it returns once the whole sort has
+ * run on the device.  Errors: PLAS_ERR_INVALID_ARG (sizes, NULL, D range,
+ * misaligned pointers), PLAS_ERR_NONFINITE (x holds NaN/Inf; nothing is
+ * written to the outputs), PLAS_ERR_OOM, PLAS_ERR_CUDA.
+ */
+int plas_sort(const float* x, int H, int W, int D, const float* weights,
+              const float* carried, int C, uint64_t seed, const plas_schedule* sched,
+              const int32_t* perm_init, plas_state* state_io, int32_t* perm_out,
+              float* carried_out, float* sorted_out, void* workspace, size_t ws_bytes,
+              plas_stats* stats, void* stream);
+
+/*
+ * plas_gather_rows -- dst[p, :] = src[perm[p], :] for p < N (Sec. 3: every
+ * attribute plane follows the one permutation).  src, dst: device N x C
+ * float32 (must not overlap); perm: device N int32 with values in [0, N)
+ * (not checked).  C >= 1.
+ */
+int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float* dst,
+                     void* stream);
+
+/*
+ * plas_target -- the low-pass target of Sec. 3.1 for one arrangement: the
+ * separable Gaussian blur of the weighted, normalised features of x[perm]
+ * at radius phi (half-width floor(phi), sigma = sigma_ratio*phi, taps
+ * truncated at the border and renormalised by the in-range tap mass).
+ * x: device N x D; perm: device N int32; T: device N x D output.
+ * weights: host D floats or NULL.  The same kernels as plas_sort's loop.
+ */
+int plas_target(const float* x, int H, int W, int D, const float* weights, int normalize,
+                const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream);
+
+/*
+ * plas_group_permutation -- the grouping permutation of Sec. 3.1 ("a random
+ * permutation of all elements from a block", shared by all blocks): out[m]
+ * for m < n, a keyed bijection of [0, n) (six-round Feistel network driven
+ * by Philox4x32-10, cycle walking).  tag/counter select the stream (3 and
+ * the iteration for groupings, 1 and 0 for the initial placement).
+ * out: device n uint32.  1 <= n <= 2^26.
+ */
+int plas_group_permutation(uint64_t seed, uint32_t tag, uint64_t counter, uint32_t n,
+                           uint32_t* out, void* stream);
+
+/*
+ * plas_philox -- Philox4x32-10 (Salmon et al., SC'11) on the device:
+ * out[4i..4i+3] = philox(ctr[4i..4i+3], key).  ctr, out: device 4n uint32.
+ */
+int plas_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out,
+                void* stream);
+
+/*
+ * plas_grid_metrics -- quality of an H x W x D grid (device, float32):
+ *   out[0] mean L2 distance over all horizontal and vertical neighbour pairs;
+ *   out[1] VAD: population variance of |a - b| over all neighbour pairs and
+ *          all channels, on values multiplied by 'scale' (supplementary,
+ *          "Sorting performance"; scale 255 for [0,1] colours);
+ *   out[2] mean |a - b| (same pairs, scaled).
+ * out: host, 3 doubles.  Waits for the stream.  FP64 accumulation.
+ */
+int plas_grid_metrics(const float* grid, int H, int W, int D, double scale, double* out,
+                      void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* smoothness loss (Sec. 3.2)                                             */
+/* ---------------------------------------------------------------------- */
+/*
+ * x: device H x W x C float32, channel-last.  B is the separable Gaussian
+ * of 'ksize' taps (odd, 1..31) with the given sigma, normalised to sum 1
+ * over the full window, with zero padding.  r = x - Bx.
+ *   loss = (1/M) * sum_{y,x,c} lam_c * r^2,   M = H*W*C
+ *   dloss/dx = (2 g / M) * lam_c * (r - B r)     (B^T = B: symmetric taps,
+ *                                                 zero padding)
+ * ch_weights: device C floats or NULL (all ones).
+ * plas_smooth_loss_fwd writes loss (device, 1 float).  It accumulates in
+ * FP64 with a fixed reduction order, so the value does not depend on
+ * scheduling.  plas_smooth_loss_bwd reads grad_loss (device scalar g) and
+ * writes grad_x (device H x W x C, must not overlap x); it recomputes r from
+ * x.  workspace: device or NULL (then allocated stream-ordered per call),
+ * at least plas_smooth_loss_workspace_bytes(H, W, C) bytes, 256-byte
+ * aligned.  Errors: PLAS_ERR_INVALID_ARG (sizes, even or too large ksize,
+ * sigma <= 0, NULL), PLAS_ERR_OOM, PLAS_ERR_CUDA.
+ */
+size_t plas_smooth_loss_workspace_bytes(int H, int W, int C);
+int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int ksize,
+                         const float* ch_weights, float* loss, void* workspace,
+                         size_t ws_bytes, void* stream);
+int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int ksize,
+                         const float* ch_weights, const float* grad_loss, float* grad_x,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* batched sort: many independent grids advanced together                 */
+/* ---------------------------------------------------------------------- */
+typedef struct plas_job {
+    const float* x;        /* device, N x D                                  */
+    int H, W;              /* grid sides                                     */
+    const float* carried;  /* device, N x C or NULL                          */
+    int C;
+    uint64_t seed;
+    int32_t* perm_out;     /* device, N                                      */
+    float* carried_out;    /* device, N x C or NULL                          */
+    plas_state* state_out; /* host or NULL: final state of this grid         */
+} plas_job;
+
+/* Device bytes plas_batch_sort needs for these jobs (all of one D). */
+size_t plas_batch_workspace_bytes(int n, const plas_job* jobs, int D);
+
+/*
+ * plas_batch_sort -- sorts n independent grids of D channels with one
+ * schedule, advancing every unfinished grid by one iteration per sweep:
+ * each sweep is one launch per kernel class over all grids, so small grids
+ * share the GPU instead of running one after another.  Every grid keeps its
+ * own counters and random streams, so each result is bit-identical to
+ * plas_sort on that grid alone with the same seed and schedule.
+ * jobs: host array of n descriptors; weights: host D floats or NULL.
+ * workspace: device, plas_batch_workspace_bytes(...) bytes, or NULL
+ * (allocated internally).  Returns PLAS_ERR_INVALID_ARG for a bad job.
+ */
+int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
+                    const plas_schedule* sched, void* workspace, size_t ws_bytes,
+                    void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* diagnostics                                                            */
+/* ---------------------------------------------------------------------- */
+const char* plas_status_string(int status);
+const char* plas_last_error(void);  /* thread-local; "" if none */
+int plas_version(void);              /* major*10000 + minor*100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLAS_H_ */

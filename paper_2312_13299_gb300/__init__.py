@@ -1,0 +1,355 @@
+"""GB300 (sm_103a) Parallel Linear Assignment Sorting and grid smoothness loss.
+
+Python binding of the C ABI in ``include/plas.h`` (Morgenstern et al., "Compact
+3D Scene Representation via Self-Organizing Gaussian Grids", arXiv 2312.13299,
+Sec. 3.1 and 3.2).  This module only marshals arguments: PyTorch provides
+device memory and the current CUDA stream, and every step of the sort and of
+the loss runs in the library's own CUDA kernels.  There is no CPU fallback; a
+missing library raises.
+
+Main entry points
+    sort(x, H, W, ...)          PLAS grid sort -> permutation (+ carried attributes)
+    batch_sort(jobs, ...)       many independent grids with one schedule
+    smooth_loss(x, ...)         Sec. 3.2 smoothness loss with a hand-written backward
+    grid_metrics(g, scale)      mean neighbour L2 and VAD of a grid
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field, fields
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import check, load
+
+__all__ = ["Schedule", "SortResult", "sort", "batch_sort", "gather_rows", "target",
+           "group_permutation", "philox", "grid_metrics", "smooth_loss", "SmoothLoss",
+           "num_levels", "sort_workspace_bytes", "load"]
+
+
+@dataclass
+class Schedule:
+    """Mirror of ``plas_schedule`` (Sec. 3.1 defaults; sigma_ratio is a reading)."""
+    phi0: float = 0.0
+    shrink: float = 0.95
+    phi_min: float = 1.0
+    tol: float = 1e-4
+    sigma_ratio: float = 0.5
+    min_block: int = 16
+    shuffle_init: bool = True
+    normalize: bool = True
+    iters_per_poll: int = 8
+    max_iters: int = 0
+    profile: bool = False
+
+    def to_c(self, trace_S: Optional[torch.Tensor] = None,
+             trace_level: Optional[torch.Tensor] = None) -> _lib.plas_schedule:
+        s = _lib.plas_schedule()
+        s.phi0, s.shrink, s.phi_min, s.tol = self.phi0, self.shrink, self.phi_min, self.tol
+        s.sigma_ratio, s.min_block = self.sigma_ratio, self.min_block
+        s.shuffle_init, s.normalize = int(self.shuffle_init), int(self.normalize)
+        s.iters_per_poll, s.max_iters, s.profile = self.iters_per_poll, self.max_iters, int(self.profile)
+        s.trace_S = trace_S.data_ptr() if trace_S is not None else None
+        s.trace_level = trace_level.data_ptr() if trace_level is not None else None
+        cap = 0
+        if trace_S is not None:
+            cap = trace_S.numel()
+        if trace_level is not None:
+            cap = min(cap, trace_level.numel()) if trace_S is not None else trace_level.numel()
+        s.trace_cap = cap
+        return s
+
+
+@dataclass
+class SortResult:
+    perm: torch.Tensor
+    carried: Optional[torch.Tensor] = None
+    sorted: Optional[torch.Tensor] = None
+    state: dict = field(default_factory=dict)
+    stats: Optional[dict] = None
+    trace_S: Optional[torch.Tensor] = None
+    trace_level: Optional[torch.Tensor] = None
+
+
+def _stream(dev: torch.device) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=torch.float32) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    return t.contiguous()
+
+
+def _weights(weights, D: int):
+    if weights is None:
+        return None
+    w = [float(v) for v in (weights.tolist() if isinstance(weights, torch.Tensor) else weights)]
+    if len(w) != D:
+        raise ValueError(f"weights must have {D} entries")
+    return (ctypes.c_float * D)(*w)
+
+
+def _state_to_c(state) -> _lib.plas_state:
+    st = _lib.plas_state()
+    if state is None:
+        return st
+    if isinstance(state, _lib.plas_state):
+        ctypes.memmove(ctypes.byref(st), ctypes.byref(state), ctypes.sizeof(st))
+        return st
+    for k, _ in _lib.plas_state._fields_:
+        if k in state:
+            setattr(st, k, state[k])
+    return st
+
+
+def _stats_to_dict(s: _lib.plas_stats) -> dict:
+    d = {k: getattr(s, k) for k, _ in _lib.plas_stats._fields_ if k != "kernel"}
+    d["kernels"] = {n: {"launches": s.kernel[i].launches, "ms": s.kernel[i].ms,
+                        "bytes": s.kernel[i].bytes, "flops": s.kernel[i].flops}
+                    for i, n in enumerate(_lib.KERNEL_NAMES)}
+    return d
+
+
+def num_levels(H: int, W: int, schedule: Optional[Schedule] = None) -> int:
+    s = (schedule or Schedule()).to_c()
+    n = load().plas_num_levels(H, W, ctypes.byref(s))
+    if n < 0:
+        check(n, "plas_num_levels")
+    return n
+
+
+def sort_workspace_bytes(H: int, W: int, D: int) -> int:
+    return int(load().plas_sort_workspace_bytes(H, W, D))
+
+
+def sort(x: torch.Tensor, H: int, W: int, weights=None, carried: Optional[torch.Tensor] = None,
+         seed: int = 0, schedule: Optional[Schedule] = None,
+         perm_init: Optional[torch.Tensor] = None, state=None, want_sorted: bool = False,
+         want_stats: bool = False, trace_cap: int = 0,
+         workspace: Optional[torch.Tensor] = None) -> SortResult:
+    """PLAS grid sort (Sec. 3.1): x [N, D] float32 on a CUDA device, N = H*W.
+
+    Returns the permutation (perm[p] = row of x placed at grid cell p), the
+    carried attributes in grid order, optionally x in grid order, the final
+    schedule state (resumable together with the permutation), statistics and
+    a per-iteration trace of the fixed-point residual sum."""
+    lib = load()
+    x = _need_cuda(x, "x")
+    if x.dim() != 2 or x.shape[0] != H * W:
+        raise ValueError("x must be [H*W, D]")
+    N, D = x.shape
+    dev = x.device
+    sched = schedule or Schedule()
+    perm = torch.empty(N, dtype=torch.int32, device=dev)
+    C = 0
+    carried_out = None
+    if carried is not None:
+        carried = _need_cuda(carried, "carried")
+        if carried.dim() != 2 or carried.shape[0] != N:
+            raise ValueError("carried must be [N, C]")
+        C = carried.shape[1]
+        carried_out = torch.empty_like(carried)
+    sorted_out = torch.empty_like(x) if want_sorted else None
+    if perm_init is not None:
+        perm_init = _need_cuda(perm_init, "perm_init", torch.int32)
+    tS = tL = None
+    if trace_cap > 0:
+        tS = torch.full((trace_cap,), -1, dtype=torch.int64, device=dev)
+        tL = torch.full((trace_cap,), -1, dtype=torch.int32, device=dev)
+    cs = sched.to_c(tS, tL)
+    st = _state_to_c(state)
+    stats = _lib.plas_stats() if want_stats else None
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    with torch.cuda.device(dev):
+        rc = lib.plas_sort(x.data_ptr(), H, W, D, _weights(weights, D),
+                           carried.data_ptr() if carried is not None else None, C, seed,
+                           ctypes.byref(cs), perm_init.data_ptr() if perm_init is not None else None,
+                           ctypes.byref(st), perm.data_ptr(),
+                           carried_out.data_ptr() if carried_out is not None else None,
+                           sorted_out.data_ptr() if sorted_out is not None else None,
+                           ws_ptr, ws_bytes, ctypes.byref(stats) if stats is not None else None,
+                           _stream(dev))
+    check(rc, "plas_sort")
+    res = SortResult(perm=perm, carried=carried_out, sorted=sorted_out, state=st.as_dict(),
+                     stats=_stats_to_dict(stats) if stats is not None else None)
+    if tS is not None:
+        it0 = int(state["it"]) if isinstance(state, dict) and "it" in state else 0
+        it1 = min(st.it, trace_cap)
+        res.trace_S = tS[it0:it1]
+        res.trace_level = tL[it0:it1]
+    return res
+
+
+def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] = None,
+               workspace: Optional[torch.Tensor] = None) -> list:
+    """Sort many independent grids (all with the same D) in one call.
+
+    jobs: dicts with x [H*W, D], H, W, optional carried [H*W, C] and seed.
+    Returns a list of SortResult (perm, carried, state)."""
+    lib = load()
+    if not jobs:
+        return []
+    D = int(jobs[0]["x"].shape[1])
+    dev = jobs[0]["x"].device
+    arr = (_lib.plas_job * len(jobs))()
+    states = [_lib.plas_state() for _ in jobs]
+    outs = []
+    keep = []
+    for i, j in enumerate(jobs):
+        x = _need_cuda(j["x"], "x")
+        H, W = int(j["H"]), int(j["W"])
+        if x.shape != (H * W, D):
+            raise ValueError("every job's x must be [H*W, D] with the same D")
+        perm = torch.empty(H * W, dtype=torch.int32, device=dev)
+        car = j.get("carried")
+        cout = None
+        if car is not None:
+            car = _need_cuda(car, "carried")
+            cout = torch.empty_like(car)
+        keep += [x, car]
+        arr[i].x, arr[i].H, arr[i].W = x.data_ptr(), H, W
+        arr[i].carried = car.data_ptr() if car is not None else None
+        arr[i].C = car.shape[1] if car is not None else 0
+        arr[i].seed = int(j.get("seed", 0))
+        arr[i].perm_out = perm.data_ptr()
+        arr[i].carried_out = cout.data_ptr() if cout is not None else None
+        arr[i].state_out = ctypes.pointer(states[i])
+        outs.append((perm, cout))
+    cs = (schedule or Schedule()).to_c()
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    with torch.cuda.device(dev):
+        rc = lib.plas_batch_sort(len(jobs), arr, D, _weights(weights, D), ctypes.byref(cs), ws_ptr,
+                                 ws_bytes, _stream(dev))
+    check(rc, "plas_batch_sort")
+    return [SortResult(perm=p, carried=c, state=s.as_dict()) for (p, c), s in zip(outs, states)]
+
+
+def gather_rows(src: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
+    """out[p] = src[perm[p]] on the device (every attribute follows the permutation)."""
+    src = _need_cuda(src, "src")
+    perm = _need_cuda(perm, "perm", torch.int32)
+    src2 = src.reshape(src.shape[0], -1)
+    out = torch.empty_like(src2)
+    with torch.cuda.device(src.device):
+        rc = load().plas_gather_rows(src2.data_ptr(), src2.shape[0], src2.shape[1], perm.data_ptr(),
+                                     out.data_ptr(), _stream(src.device))
+    check(rc, "plas_gather_rows")
+    return out.reshape(src.shape)
+
+
+def target(x: torch.Tensor, H: int, W: int, perm: torch.Tensor, phi: float, weights=None,
+           normalize: bool = True, sigma_ratio: float = 0.5) -> torch.Tensor:
+    """Low-pass target of one arrangement (the blur step of Sec. 3.1) -> [H, W, D]."""
+    x = _need_cuda(x, "x")
+    perm = _need_cuda(perm, "perm", torch.int32)
+    N, D = x.shape
+    T = torch.empty((H, W, D), dtype=torch.float32, device=x.device)
+    with torch.cuda.device(x.device):
+        rc = load().plas_target(x.data_ptr(), H, W, D, _weights(weights, D), int(normalize),
+                                perm.data_ptr(), float(phi), float(sigma_ratio), T.data_ptr(),
+                                _stream(x.device))
+    check(rc, "plas_target")
+    return T
+
+
+def group_permutation(seed: int, tag: int, counter: int, n: int,
+                      device="cuda") -> torch.Tensor:
+    """Keyed permutation of [0, n) as int32 tensor (bits of the uint32 values)."""
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    with torch.cuda.device(out.device):
+        rc = load().plas_group_permutation(seed, tag, counter, n, out.data_ptr(),
+                                           _stream(out.device))
+    check(rc, "plas_group_permutation")
+    return out
+
+
+def philox(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
+    """Philox4x32-10 of n counters ([n, 4] int32 bit patterns) -> [n, 4] int32."""
+    ctr = _need_cuda(ctr, "ctr", torch.int32)
+    out = torch.empty_like(ctr)
+    with torch.cuda.device(ctr.device):
+        rc = load().plas_philox(ctr.data_ptr(), key0, key1, ctr.shape[0], out.data_ptr(),
+                                _stream(ctr.device))
+    check(rc, "plas_philox")
+    return out
+
+
+def grid_metrics(grid: torch.Tensor, scale: float = 1.0):
+    """(mean neighbour L2, VAD of values*scale, mean |diff|*scale) of [H, W, D]."""
+    grid = _need_cuda(grid, "grid")
+    H, W, D = grid.shape
+    out = (ctypes.c_double * 3)()
+    with torch.cuda.device(grid.device):
+        rc = load().plas_grid_metrics(grid.data_ptr(), H, W, D, float(scale), out,
+                                      _stream(grid.device))
+    check(rc, "plas_grid_metrics")
+    return out[0], out[1], out[2]
+
+
+def _lam_ptr(lam: Optional[torch.Tensor]):
+    return lam.data_ptr() if lam is not None else None
+
+
+def smooth_loss_fwd(x: torch.Tensor, sigma: float = 1.0, ksize: int = 7,
+                    lam: Optional[torch.Tensor] = None) -> torch.Tensor:
+    x = _need_cuda(x, "x")
+    H, W, C = x.shape
+    if lam is not None:
+        lam = _need_cuda(lam, "lam")
+    loss = torch.empty((), dtype=torch.float32, device=x.device)
+    with torch.cuda.device(x.device):
+        rc = load().plas_smooth_loss_fwd(x.data_ptr(), H, W, C, float(sigma), int(ksize),
+                                         _lam_ptr(lam), loss.data_ptr(), None, 0,
+                                         _stream(x.device))
+    check(rc, "plas_smooth_loss_fwd")
+    return loss
+
+
+def smooth_loss_bwd(x: torch.Tensor, grad_loss: torch.Tensor, sigma: float = 1.0,
+                    ksize: int = 7, lam: Optional[torch.Tensor] = None) -> torch.Tensor:
+    x = _need_cuda(x, "x")
+    H, W, C = x.shape
+    if lam is not None:
+        lam = _need_cuda(lam, "lam")
+    g = _need_cuda(grad_loss.reshape(()).to(torch.float32), "grad_loss")
+    grad = torch.empty_like(x)
+    with torch.cuda.device(x.device):
+        rc = load().plas_smooth_loss_bwd(x.data_ptr(), H, W, C, float(sigma), int(ksize),
+                                         _lam_ptr(lam), g.data_ptr(), grad.data_ptr(), None, 0,
+                                         _stream(x.device))
+    check(rc, "plas_smooth_loss_bwd")
+    return grad
+
+
+class SmoothLoss(torch.autograd.Function):
+    """Sec. 3.2 smoothness loss L = mean(lam_c (x - Bx)^2) with a hand-written
+    backward kernel.  x: [H, W, C] float32 CUDA, channel-last."""
+
+    @staticmethod
+    def forward(ctx, x, sigma=1.0, ksize=7, lam=None):
+        ctx.sigma, ctx.ksize = sigma, ksize
+        ctx.save_for_backward(x, lam) if lam is not None else ctx.save_for_backward(x)
+        ctx.has_lam = lam is not None
+        return smooth_loss_fwd(x, sigma, ksize, lam)
+
+    @staticmethod
+    def backward(ctx, g):
+        if ctx.has_lam:
+            x, lam = ctx.saved_tensors
+        else:
+            (x,), lam = ctx.saved_tensors, None
+        return smooth_loss_bwd(x, g, ctx.sigma, ctx.ksize, lam), None, None, None
+
+
+def smooth_loss(x: torch.Tensor, sigma: float = 1.0, ksize: int = 7,
+                lam: Optional[torch.Tensor] = None) -> torch.Tensor:
+    return SmoothLoss.apply(x, sigma, ksize, lam)

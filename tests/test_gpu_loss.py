@@ -1,0 +1,63 @@
+"""GPU smoothness loss (Sec. 3.2) against the FP64 oracle and finite
+differences.  Bar (floating point): loss within 1e-5 relative; gradient with
+||g_gpu - g_64|| <= 1e-5 ||g_64|| and max|g_gpu - g_64| <= 1e-5 max|g_64|."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_13299_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(plas, orc, x, sigma, ksize, lam=None, g=1.0):
+    xc = torch.from_numpy(x).cuda().requires_grad_(True)
+    lc = torch.from_numpy(lam).cuda() if lam is not None else None
+    L = plas.smooth_loss(xc, sigma, ksize, lc)
+    (L * g).backward()
+    L64, g64 = orc.smooth_loss64(x.astype(np.float64), sigma, ksize, lam, grad_loss=g)
+    assert abs(L.item() - L64) <= 1e-5 * abs(L64)
+    gg = xc.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g64) <= 1e-5 * np.linalg.norm(g64)
+    assert np.abs(gg - g64).max() <= 1e-5 * np.abs(g64).max()
+
+
+@pytest.mark.parametrize("H,W,C,sigma,ksize", [(16, 16, 3, 1.0, 7), (37, 45, 5, 1.0, 7),
+                                               (64, 64, 59, 1.0, 7), (33, 70, 14, 3.0, 5),
+                                               (8, 200, 1, 2.0, 31), (100, 31, 2, 0.7, 3)])
+def test_loss_matches_fp64(plas, orc, H, W, C, sigma, ksize):
+    x = np.random.default_rng(H + W + C).random((H, W, C), dtype=np.float32)
+    lam = (np.random.default_rng(1).random(C) + 0.5).astype(np.float32)
+    _check(plas, orc, x, sigma, ksize)
+    _check(plas, orc, x, sigma, ksize, lam, g=0.37)
+
+
+def test_loss_full_size_1024x1024x59(plas, orc):
+    x = synth.loss_grid(1024, 1024, seed=0).astype(np.float32)
+    _check(plas, orc, x, 1.0, 7)
+
+
+def test_loss_gradient_finite_differences(plas, orc):
+    """Central differences of the FP64 loss at sampled points vs the GPU gradient."""
+    x = np.random.default_rng(5).random((24, 24, 4), dtype=np.float32)
+    xc = torch.from_numpy(x).cuda().requires_grad_(True)
+    plas.smooth_loss(xc, 1.0, 7).backward()
+    g = xc.grad.cpu().numpy()
+    x64 = x.astype(np.float64)
+    rng = np.random.default_rng(6)
+    h = 1e-6
+    for _ in range(30):
+        i = tuple(rng.integers(0, s) for s in x.shape)
+        xp, xm = x64.copy(), x64.copy()
+        xp[i] += h
+        xm[i] -= h
+        fd = (orc.smooth_loss64(xp, 1.0, 7, want_grad=False)[0]
+              - orc.smooth_loss64(xm, 1.0, 7, want_grad=False)[0]) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * np.abs(g).max()
+
+
+def test_loss_deterministic(plas):
+    x = torch.rand(256, 256, 59, device="cuda")
+    a = plas.smooth_loss_fwd(x)
+    b = plas.smooth_loss_fwd(x)
+    assert torch.equal(a, b)

@@ -1,0 +1,204 @@
+"""GPU parity of the PLAS sort against the CPU oracle (through the C ABI).
+
+Bar: bit-exact.  The permutation, the per-iteration fixed-point residual sum
+and the final schedule state of the CUDA path equal the oracle's on the same
+seeded inputs: Philox outputs, grouping permutations, blur targets (several
+tiles, ragged tails, multi-chunk radii), full sorts of small and ragged grids,
+and single iterations resumed from GPU snapshots of the full-size workloads
+(512^2, 1024^2, 1448^2 x 14 channels) at large, middle and small radii.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_13299_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def test_philox_bitexact(plas, orc):
+    rng = np.random.default_rng(0)
+    n = 5000
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0x12345678, 0x9ABCDEF0]
+    got = plas.philox(_cuda(ctr.view(np.int32)), key[0], key[1]).cpu().numpy().view(np.uint32)
+    for i in range(0, n, 7):
+        assert np.array_equal(got[i], orc.philox(ctr[i], key))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 15, 16, 255, 256, 257, 1023, 4096, 65536, 262144])
+def test_group_permutation_bitexact(plas, orc, n):
+    for tag, ctr in [(3, 0), (3, 12345), (1, 0)]:
+        got = plas.group_permutation(77, tag, ctr, n).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, orc.prp_table(77, tag, ctr, n))
+
+
+TARGET_CASES = [(64, 64, 3, 31.0), (37, 53, 3, 17.3), (80, 96, 14, 39.5), (64, 64, 14, 1.0),
+                (200, 130, 3, 64.9), (17, 300, 2, 8.0), (300, 17, 5, 8.0), (1, 50, 3, 1.0),
+                (50, 1, 3, 1.0), (129, 257, 14, 128.5), (400, 64, 1, 199.0), (24, 24, 16, 11.0)]
+
+
+@pytest.mark.parametrize("H,W,D,phi", TARGET_CASES)
+def test_target_bitexact(plas, orc, H, W, D, phi):
+    rng = np.random.default_rng(H * 1000 + W)
+    x = rng.random((H * W, D), dtype=np.float32)
+    perm = rng.permutation(H * W).astype(np.int32)
+    w = (rng.random(D) + 0.5).astype(np.float32)
+    got = plas.target(_cuda(x), H, W, _cuda(perm), phi, weights=w).cpu().numpy()
+    want = orc.target(x, H, W, perm, phi, weights=w)
+    assert np.array_equal(got, want)
+
+
+def _sched(plas, **kw):
+    return plas.Schedule(**kw)
+
+
+def _compare_full(plas, orc, x, H, W, seed, weights=None, cap=1 << 15, **kw):
+    want = orc.sort(x, H, W, weights=weights, seed=seed, sched=orc.default_schedule(**kw))
+    got = plas.sort(_cuda(x), H, W, weights=weights, seed=seed, schedule=_sched(plas, **kw),
+                    trace_cap=cap)
+    assert np.array_equal(got.perm.cpu().numpy(), want["perm"])
+    n = want["iterations"]
+    assert got.state["it"] == n
+    assert np.array_equal(got.trace_S.cpu().numpy(), want["trace_S"])
+    assert np.array_equal(got.trace_level.cpu().numpy(), want["trace_level"])
+    ws = want["state"]
+    for k in ["it", "epoch", "redraws", "level", "stall", "has_prev", "done", "d_prev", "d_last",
+              "scale_exp"]:
+        assert got.state[k] == getattr(ws, k), k
+    return got, want
+
+
+def test_full_sort_64x64x3(plas, orc):
+    """The small workload end to end (64x64 RGB, seed 0, default schedule)."""
+    x = synth.rgb_uniform(64, seed=0)
+    _compare_full(plas, orc, x, 64, 64, 0)
+
+
+@pytest.mark.parametrize("H,W,D,seed", [(37, 53, 3, 1), (48, 80, 14, 2), (16, 16, 1, 3),
+                                        (2, 2, 3, 4), (3, 3, 3, 5), (1, 1, 3, 6), (1, 7, 3, 7),
+                                        (7, 1, 3, 8), (20, 33, 5, 9), (96, 40, 4, 10)])
+def test_full_sort_ragged_and_degenerate(plas, orc, H, W, D, seed):
+    x = np.random.default_rng(seed).random((H * W, D), dtype=np.float32)
+    _compare_full(plas, orc, x, H, W, seed)
+
+
+def test_full_sort_weights_unnormalized_and_no_shuffle(plas, orc):
+    rng = np.random.default_rng(11)
+    x = (rng.normal(size=(40 * 44, 6)) * [1, 5, 0.1, 2, 3, 1]).astype(np.float32)
+    w = np.array([1.0, 0.5, 3.0, 0.0, 2.0, -1.5], np.float32)
+    _compare_full(plas, orc, x, 40, 44, 12, weights=w)
+    _compare_full(plas, orc, x, 40, 44, 12, weights=w, normalize=0)
+    _compare_full(plas, orc, x, 40, 44, 12, shuffle_init=0, tol=1e-3, sigma_ratio=1.0)
+
+
+def test_3dgs_shaped_full_sort_with_carried(plas, orc):
+    x, car = synth.gaussians_3dgs(48 * 48, seed=3)
+    got, want = _compare_full(plas, orc, x, 48, 48, 3)
+    res = plas.sort(_cuda(x), 48, 48, carried=_cuda(car), seed=3, want_sorted=True)
+    perm = want["perm"]
+    assert np.array_equal(res.perm.cpu().numpy(), perm)
+    assert np.array_equal(res.carried.cpu().numpy(), orc.gather(car, perm))
+    assert np.array_equal(res.sorted.cpu().numpy(), orc.gather(x, perm))
+
+
+def test_empty_grid(plas):
+    x = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    r = plas.sort(x, 0, 0)
+    assert r.perm.numel() == 0 and r.state["done"] == 1
+
+
+def test_poll_batch_size_does_not_change_result(plas):
+    x = _cuda(synth.rgb_uniform(40, seed=4))
+    a = plas.sort(x, 40, 40, seed=4, schedule=plas.Schedule(iters_per_poll=1)).perm
+    b = plas.sort(x, 40, 40, seed=4, schedule=plas.Schedule(iters_per_poll=37)).perm
+    c = plas.sort(x, 40, 40, seed=4).perm
+    assert torch.equal(a, b) and torch.equal(a, c)
+
+
+def _snapshot_parity(plas, orc, side, seed, radii, iters_before=2):
+    """GPU runs to the first iteration of the level nearest each radius, then the
+    oracle and the GPU each run one (or a few) iterations from that snapshot."""
+    x, _ = synth.gaussians_3dgs(side * side, seed=seed, with_carried=False)
+    xc = _cuda(x)
+    phis = orc.levels(side, side)
+    full = plas.sort(xc, side, side, seed=seed, trace_cap=200000)
+    tl = full.trace_level.cpu().numpy()
+    for phi in radii:
+        L = int(np.argmin(np.abs(phis - phi)))
+        start = int(np.nonzero(tl == L)[0][0]) + iters_before
+        snap = plas.sort(xc, side, side, seed=seed, schedule=plas.Schedule(max_iters=start))
+        st = dict(snap.state)
+        perm0 = snap.perm.cpu().numpy()
+        ost = orc.State()
+        for k, v in st.items():
+            if hasattr(ost, k):
+                setattr(ost, k, v)
+        want = orc.sort(x, side, side, seed=seed, sched=orc.default_schedule(max_iters=start + 1),
+                        perm_in=perm0, state=ost)
+        got = plas.sort(xc, side, side, seed=seed, schedule=plas.Schedule(max_iters=start + 1),
+                        perm_init=snap.perm, state=st, trace_cap=start + 2)
+        assert np.array_equal(got.perm.cpu().numpy(), want["perm"]), (side, phi)
+        assert got.state["d_last"] == want["state"].d_last
+        assert got.trace_S.cpu().numpy().tolist() == want["trace_S"].tolist()
+        # the uninterrupted GPU run took the same step
+        assert int(full.trace_S[start].item()) == int(want["trace_S"][0])
+
+
+@pytest.mark.parametrize("side,radii", [(512, [255, 60, 10, 1]), (1024, [511, 100, 10, 1]),
+                                        (1448, [723, 10, 1])])
+def test_snapshot_parity_full_size(plas, orc, side, radii):
+    _snapshot_parity(plas, orc, side, side, radii)
+
+
+def test_nonfinite_input_rejected(plas):
+    x = torch.rand(32 * 32, 3, device="cuda")
+    x[100, 1] = float("nan")
+    with pytest.raises(RuntimeError) as e:
+        plas.sort(x, 32, 32)
+    assert "NaN" in str(e.value)
+
+
+def test_invalid_arguments(plas):
+    x = torch.rand(32 * 32, 3, device="cuda")
+    with pytest.raises(ValueError):
+        plas.sort(x, 32, 31)
+    with pytest.raises(RuntimeError):
+        plas.sort(torch.rand(16, 17, device="cuda"), 4, 4)  # D = 17 is not supported
+    with pytest.raises(RuntimeError):
+        plas.sort(x, 32, 32, schedule=plas.Schedule(shrink=1.5))
+
+
+def test_grid_metrics(plas, orc):
+    g = np.random.default_rng(2).random((61, 47, 5), dtype=np.float32)
+    nl2, vad, _ = plas.grid_metrics(_cuda(g), 255.0)
+    onl2, ovad = orc.metrics(g, 255.0)
+    assert abs(nl2 - onl2) <= 1e-9 * onl2 and abs(vad - ovad) <= 1e-9 * ovad
+
+
+def test_gather_rows(plas, orc):
+    rng = np.random.default_rng(3)
+    for C in [1, 3, 4, 45, 64]:
+        src = rng.random((1000, C), dtype=np.float32)
+        perm = rng.permutation(1000).astype(np.int32)
+        got = plas.gather_rows(_cuda(src), _cuda(perm)).cpu().numpy()
+        assert np.array_equal(got, orc.gather(src, perm))
+
+
+def test_batch_equals_individual(plas):
+    jobs = []
+    for i, (H, W) in enumerate([(40, 40), (17, 64), (64, 17), (33, 33)]):
+        x, c = synth.gaussians_3dgs(H * W, seed=i)
+        jobs.append({"x": _cuda(x), "H": H, "W": W, "carried": _cuda(c), "seed": 100 + i})
+    res = plas.batch_sort(jobs)
+    for j, r in zip(jobs, res):
+        one = plas.sort(j["x"], j["H"], j["W"], carried=j["carried"], seed=j["seed"])
+        assert torch.equal(r.perm, one.perm) and torch.equal(r.carried, one.carried)
+        assert r.state["it"] == one.state["it"]
