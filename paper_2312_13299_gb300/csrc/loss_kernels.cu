@@ -137,7 +137,7 @@ static int check_args(const float* x, int H, int W, int C, float sigma, int ksiz
         return PLAS_ERR_INVALID_ARG;
     }
     if (!(sigma > 0.0f)) { plas::set_last_error("sigma must be > 0"); return PLAS_ERR_INVALID_ARG; }
-    if (smem_bytes(C, ksize / 2) > 227 * 1024) { plas::set_last_error("too many channels"); return PLAS_ERR_INVALID_ARG; }
+    if (smem_bytes(C, ksize / 2) > 200 * 1024) { plas::set_last_error("too many channels"); return PLAS_ERR_INVALID_ARG; }
     return PLAS_OK;
 }
 
@@ -162,15 +162,13 @@ static size_t ws_bytes_for(int H, int W, int C) {
     return part + (size_t)H * W * C * sizeof(float);
 }
 
+// Dynamic shared memory above 48 KB needs an opt-in; request exactly what the
+// launch uses (the kernel also has a little static shared memory).
 template <bool GRAD>
-static void set_smem_attr(size_t bytes) {
-    static int done_dev[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && done_dev[dev]) return;
-    cudaFuncSetAttribute(smooth_kernel<GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (dev >= 0 && dev < 64) done_dev[dev] = 1;
-    (void)bytes;
+static bool set_smem_attr(size_t bytes) {
+    if (bytes <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(smooth_kernel<GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes) == cudaSuccess;
 }
 
 }  // namespace plas_loss
@@ -205,7 +203,12 @@ int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int k
     }
     const int h = ksize / 2;
     const size_t sm = smem_bytes(C, h);
-    set_smem_attr<false>(sm);
+    if (!set_smem_attr<false>(sm)) {
+        cudaGetLastError();
+        if (!workspace) cudaFreeAsync(mem, st);
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return PLAS_ERR_INVALID_ARG;
+    }
     const double inv_m = 1.0 / ((double)H * W * C);
     smooth_kernel<false><<<g, kThreads, sm, st>>>(x, H, W, C, h, make_taps(sigma, ksize), ch_weights,
                                                   nullptr, nullptr, inv_m, (double*)mem);
@@ -242,8 +245,12 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
     float* r = (float*)((char*)mem + part);
     const int h = ksize / 2;
     const size_t sm = smem_bytes(C, h);
-    set_smem_attr<false>(sm);
-    set_smem_attr<true>(sm);
+    if (!set_smem_attr<false>(sm) || !set_smem_attr<true>(sm)) {
+        cudaGetLastError();
+        if (!workspace) cudaFreeAsync(mem, st);
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return PLAS_ERR_INVALID_ARG;
+    }
     const double inv_m = 1.0 / ((double)H * W * C);
     const Taps tp = make_taps(sigma, ksize);
     // pass 1: r = x - B x (the weighted residual sum is produced as a by-product)
