@@ -416,6 +416,20 @@ def run_reference(args):
         pg.destroy_process_group()
 
 
+def run_ncu_case(args):
+    """A bounded launch sequence for profiler captures: the workload's inputs,
+    one sort capped at --ncu-case iterations (all at the top radius levels)."""
+    import torch
+    import paper_2312_13299_gb300 as plas
+    plas.load()
+    wl = WORKLOADS[args.workload]
+    side = wl["side"]
+    x_np, _ = make_inputs(wl, seed=0)
+    x = torch.from_numpy(x_np).cuda()
+    plas.sort(x, side, side, seed=0, schedule=plas.Schedule(max_iters=args.ncu_case))
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,7 +438,13 @@ def main():
     ap.add_argument("--impl", default="plas", choices=["plas", "reference"])
     ap.add_argument("--workload", default="m1", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
+                    help="run one sort of the workload capped at ITERS iterations and exit "
+                         "(a small, bounded program for ncu captures; prints nothing)")
     args = ap.parse_args()
+    if args.ncu_case > 0:
+        run_ncu_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
