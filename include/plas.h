@@ -262,6 +262,28 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
                          const float* ch_weights, const float* grad_loss, float* grad_x,
                          void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * plas_smooth_loss_fwd_noalloc -- the same loss as plas_smooth_loss_fwd, for
+ * callers that cannot allocate device memory during the call: a host loop
+ * whose memory is owned by another allocator with a fixed budget, or a
+ * latency-critical loop where cudaMalloc (which may synchronise the device)
+ * is not allowed.  The paper has no counterpart; it is a deployment variant.
+ *
+ * The per-CTA partial sums use a 512 KB array of static device memory inside
+ * the library (held on every GPU that loads the library until the process
+ * exits).  Limit: ceil(W/32) * ceil(H/32) <= 65536 (e.g. grids up to
+ * 8192 x 8192); larger grids return PLAS_ERR_INVALID_ARG.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Arguments, layout and errors as for
+ * plas_smooth_loss_fwd.
+ */
+int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigma, int ksize,
+                                 const float* ch_weights, float* loss, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* batched sort: many independent grids advanced together                 */
 /* ---------------------------------------------------------------------- */

@@ -85,6 +85,8 @@ SIGNATURES = {
                                      c_void_p, c_void_p, c_size_t, c_void_p]),
     "plas_smooth_loss_bwd": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "plas_smooth_loss_fwd_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int,
+                                             c_void_p, c_void_p, c_void_p]),
     "plas_batch_workspace_bytes": (c_size_t, [c_int, P(plas_job), c_int]),
     "plas_batch_sort": (c_int, [c_int, P(plas_job), c_int, P(c_float), P(plas_schedule),
                                 c_void_p, c_size_t, c_void_p]),

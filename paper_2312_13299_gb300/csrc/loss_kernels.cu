@@ -171,6 +171,37 @@ static bool set_smem_attr(size_t bytes) {
                                 (int)bytes) == cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free forward: the per-CTA partial sums live in this file-scope
+// device array instead of caller or stream-ordered memory.  Every GPU that
+// loads the library holds it (512 KB) until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPartials = 65536;  // (ceil(W/32) * ceil(H/32)) limit
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
+
+// Device address of g_noalloc_partials for the current device.  In host code
+// the symbol is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+static double* noalloc_partials(int* err) {
+    static double* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = PLAS_ERR_CUDA;
+        return nullptr;
+    }
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess) {
+            cudaGetLastError();
+            *err = PLAS_ERR_CUDA;
+            return nullptr;
+        }
+        addr[dev] = (double*)p;
+    }
+    *err = PLAS_OK;
+    return addr[dev];
+}
+
 }  // namespace plas_loss
 
 using namespace plas_loss;
@@ -261,6 +292,44 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
                                                  inv_m, nullptr);
     cudaError_t e = cudaGetLastError();
     if (!workspace) cudaFreeAsync(mem, st);
+    if (e != cudaSuccess) {
+        plas::set_last_error(cudaGetErrorString(e));
+        return PLAS_ERR_CUDA;
+    }
+    return PLAS_OK;
+}
+
+// Same result as plas_smooth_loss_fwd; allocates nothing (see plas.h).
+int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigma, int ksize,
+                                 const float* ch_weights, float* loss, void* stream) {
+    if (int e = check_args(x, H, W, C, sigma, ksize)) return e;
+    if (!loss) { plas::set_last_error("loss is NULL"); return PLAS_ERR_INVALID_ARG; }
+    const dim3 g = grid_of(H, W);
+    if ((long long)g.x * g.y > kNoAllocMaxPartials) {
+        plas::set_last_error("grid too large for the allocation-free loss: "
+                             "ceil(W/32)*ceil(H/32) must be <= 65536");
+        return PLAS_ERR_INVALID_ARG;
+    }
+    int err = PLAS_OK;
+    double* partials = noalloc_partials(&err);
+    if (!partials) {
+        plas::set_last_error("cudaGetSymbolAddress failed for the loss scratch array");
+        return err;
+    }
+    const int h = ksize / 2;
+    const size_t sm = smem_bytes(C, h);
+    if (!set_smem_attr<false>(sm)) {
+        cudaGetLastError();
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return PLAS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double inv_m = 1.0 / ((double)H * W * C);
+    // every CTA writes its own partial, so the array needs no clearing
+    smooth_kernel<false><<<g, kThreads, sm, st>>>(x, H, W, C, h, make_taps(sigma, ksize), ch_weights,
+                                                  nullptr, nullptr, inv_m, partials);
+    finish_loss_kernel<<<1, 1024, 0, st>>>(partials, (int)(g.x * g.y), inv_m, loss);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         plas::set_last_error(cudaGetErrorString(e));
         return PLAS_ERR_CUDA;
