@@ -70,8 +70,8 @@ class State(ctypes.Structure):
 
 def default_schedule(**kw) -> Schedule:
     """Defaults: phi0 = w/2-1, shrink 0.95, stop below 1 (Sec. 3.1); tol 1e-4
-    (supplementary); min block 16 (Sec. 3.1); sigma = phi/2 (paper silent)."""
-    s = Schedule(phi0=0.0, shrink=0.95, phi_min=1.0, tol=1e-4, sigma_ratio=0.5,
+    (supplementary); min block 16 (Sec. 3.1); sigma = 2 phi (paper silent)."""
+    s = Schedule(phi0=0.0, shrink=0.95, phi_min=1.0, tol=1e-4, sigma_ratio=2.0,
                  min_block=16, shuffle_init=1, normalize=1, pad_=0, max_iters=0)
     for k, v in kw.items():
         setattr(s, k, v)
@@ -253,7 +253,7 @@ def sort(x: np.ndarray, H: int, W: int, weights=None, seed: int = 0,
 
 
 def target(x: np.ndarray, H: int, W: int, perm, phi: float, weights=None,
-           normalize_: bool = True, sigma_ratio: float = 0.5) -> np.ndarray:
+           normalize_: bool = True, sigma_ratio: float = 2.0) -> np.ndarray:
     x = _f32(x).reshape(H * W, -1)
     D = x.shape[1]
     w = None if weights is None else _f32(weights)

@@ -238,26 +238,28 @@ static float orc_fir_at(const float* src, long step, int len, int pos, int r, co
     return acc / nrm;
 }
 
-/* G: H x W cells, cell stride gs floats, features at [0, D).  T: H x W x D. */
+/* G: H x W cells, cell stride gs floats, features at [0, D).  T: H x W x D.
+ * The first pass runs along y (columns), the second along x (rows); each
+ * divides by its own in-range tap mass. */
 void orc_blur(const float* G, int gs, int H, int W, int D, int r, double sigma, float* T)
 {
     float* taps = (float*)malloc(sizeof(float) * (size_t)(2 * r + 1));
     float* H1 = (float*)malloc(sizeof(float) * (size_t)H * W * D);
     orc_taps(r, sigma, taps);
-    /* pass 1: along x */
+    /* pass 1: along y */
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             for (int d = 0; d < D; ++d)
                 H1[((long)y * W + x) * D + d] =
-                    orc_fir_at(G + (long)y * W * gs + d, gs, W, x, r, taps);
-    /* pass 2: along y */
+                    orc_fir_at(G + (long)x * gs + d, (long)W * gs, H, y, r, taps);
+    /* pass 2: along x */
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             for (int d = 0; d < D; ++d)
                 T[((long)y * W + x) * D + d] =
-                    orc_fir_at(H1 + (long)x * D + d, (long)W * D, H, y, r, taps);
+                    orc_fir_at(H1 + (long)y * W * D + d, D, W, x, r, taps);
     free(H1);
     free(taps);
 }

@@ -21,8 +21,8 @@ def _ref_blur(G, r, sigma):
     ones = np.ones((H, W), np.float64)
     mx = ndimage.correlate1d(ones, k, axis=1, mode="constant", cval=0.0)
     my = ndimage.correlate1d(ones, k, axis=0, mode="constant", cval=0.0)
-    t = ndimage.correlate1d(G.astype(np.float64), k, axis=1, mode="constant") / mx[..., None]
-    t = ndimage.correlate1d(t, k, axis=0, mode="constant") / my[..., None]
+    t = ndimage.correlate1d(G.astype(np.float64), k, axis=0, mode="constant") / my[..., None]
+    t = ndimage.correlate1d(t, k, axis=1, mode="constant") / mx[..., None]
     return t
 
 
