@@ -416,6 +416,85 @@ def run_reference(args):
         pg.destroy_process_group()
 
 
+def run_serve(args):
+    """Served stream: n requests with Poisson arrivals (sides U{128..1024}, 14
+    sort + 45 carried channels), continuous batching under a 40 GB admission
+    budget vs the plain path (one plas_sort per request, first come first
+    served).  Latency = completion time - arrival time (host clock)."""
+    import numpy as np
+    import torch
+    import paper_2312_13299_gb300 as plas
+    from paper_2312_13299_gb300 import synth
+    plas.load()
+    dev = torch.device("cuda", 0)
+    n = args.requests
+    # offered load: arrivals at 0.8 x the plain path's service rate (measured
+    # on a 576x576 request, the mean cell count of U{128..1024} sides)
+    xm, cm = synth.gaussians_3dgs(576 * 576, seed=999)
+    xm_t, cm_t = torch.from_numpy(xm).to(dev), torch.from_numpy(cm).to(dev)
+    plas.sort(xm_t, 576, 576, carried=cm_t)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plas.sort(xm_t, 576, 576, carried=cm_t)
+    torch.cuda.synchronize()
+    mean_service = time.perf_counter() - t
+    rate = 0.8 / mean_service
+    stream = synth.request_stream(n, seed=0, rate_per_s=rate)
+    reqs = []
+    for i, (arr, side) in enumerate(stream):
+        x, c = synth.gaussians_3dgs(side * side, seed=1000 + i)
+        reqs.append((arr, side, torch.from_numpy(x).to(dev), torch.from_numpy(c).to(dev), i))
+    torch.cuda.synchronize()
+
+    def plain():
+        lat, t0, cells_iters = [], time.perf_counter(), 0
+        for arr, side, x, c, i in reqs:
+            while time.perf_counter() - t0 < arr:
+                time.sleep(0.0005)
+            r = plas.sort(x, side, side, carried=c, seed=i)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0 - arr)
+            cells_iters += side * side * r.state["it"]
+        return lat, time.perf_counter() - t0, cells_iters
+
+    def served():
+        srv = plas.Server(14, mem_budget=40 * 10 ** 9)
+        lat, t0, nxt, pending, cells_iters = {}, time.perf_counter(), 0, {}, 0
+        while len(lat) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and reqs[nxt][0] <= now:
+                arr, side, x, c, i = reqs[nxt]
+                pending[srv.submit(x, side, side, c, seed=i)] = (arr, side)
+                nxt += 1
+            if not pending:
+                time.sleep(0.0005)
+                continue
+            for tk, res in srv.step(sweeps=args.sweeps):
+                arr, side = pending.pop(tk)
+                lat[tk] = time.perf_counter() - t0 - arr
+                cells_iters += side * side * res.state["it"]
+        srv.close()
+        return list(lat.values()), time.perf_counter() - t0, cells_iters
+
+    out = {}
+    for name, fn in [("plain", plain), ("served", served)]:
+        lat, wall, ci = fn()
+        lat = np.array(lat) * 1e3
+        out[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 1),
+                     "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                     "mean_ms": round(float(lat.mean()), 1), "wall_s": round(wall, 2),
+                     "requests_per_s": round(n / wall, 3),
+                     "melem_iter_per_s": round(ci / wall / 1e6, 1)}
+    line = {"metric": "served p50/p99 latency of PLAS sort requests", "value": out["served"]["p99_ms"],
+            "unit": "ms (p99, served)", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic (seeded numpy; 3DGS-shaped attributes)",
+            "config": {"workload": f"{n} requests, Poisson arrivals at 0.8 x plain service rate "
+                                   f"({rate:.2f}/s), sides U{{128..1024}}, 14 sort + 45 carried fp32, "
+                                   "40 GB admission budget", "sweeps_per_step": args.sweeps},
+            "served": out["served"], "plain": out["plain"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(args):
     """A bounded launch sequence for profiler captures: the workload's inputs,
     one sort capped at --ncu-case iterations (all at the top radius levels)."""
@@ -426,8 +505,14 @@ def run_ncu_case(args):
     side = wl["side"]
     x_np, _ = make_inputs(wl, seed=0)
     x = torch.from_numpy(x_np).cuda()
-    plas.sort(x, side, side, seed=0, schedule=plas.Schedule(max_iters=args.ncu_case))
+    r = plas.sort(x, side, side, seed=0,
+                  schedule=plas.Schedule(max_iters=args.ncu_case, phi0=args.phi0),
+                  trace_cap=(1 << 20) if args.trace_out else 0)
     torch.cuda.synchronize()
+    if args.trace_out:
+        # level of every iteration, to attribute a launch list to radius levels
+        with open(args.trace_out, "w") as f:
+            f.write(" ".join(str(int(v)) for v in r.trace_level.cpu().tolist()))
 
 
 def main():
@@ -441,9 +526,20 @@ def main():
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="run one sort of the workload capped at ITERS iterations and exit "
                          "(a small, bounded program for ncu captures; prints nothing)")
+    ap.add_argument("--trace-out", default="", help="with --ncu-case: write the level of every "
+                    "iteration to this file")
+    ap.add_argument("--phi0", type=float, default=0.0, help="with --ncu-case: start radius "
+                    "(0 = the schedule's default), to profile small radii directly")
+    ap.add_argument("--serve", action="store_true",
+                    help="served-stream benchmark (continuous batching vs plain), own JSON line")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
     args = ap.parse_args()
     if args.ncu_case > 0:
         run_ncu_case(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -54,8 +54,9 @@ typedef struct plas_schedule {
     double phi_min;     /* the sort ends when phi falls below this, 1.0      */
     double tol;         /* relative improvement below which an assignment    */
                         /* counts as a stall, 1e-4 (supplementary)           */
-    double sigma_ratio; /* Gaussian sigma = sigma_ratio * phi; the blur      */
-                        /* half-width is floor(phi) (paper silent on sigma)  */
+    double sigma_ratio; /* Gaussian sigma = sigma_ratio * phi, default 2.0;  */
+                        /* the blur half-width is floor(phi) (the paper      */
+                        /* fixes neither)                                    */
     int min_block;      /* smallest block side beta, 16 (Sec. 3.1)           */
     int shuffle_init;   /* 1: random initial placement (Sec. 3.1); 0: start  */
                         /* from the identity (or from perm_init)             */
@@ -315,6 +316,42 @@ size_t plas_batch_workspace_bytes(int n, const plas_job* jobs, int D);
 int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
                     const plas_schedule* sched, void* workspace, size_t ws_bytes,
                     void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* served sorts: continuous batching under a device-memory budget          */
+/* ---------------------------------------------------------------------- */
+/*
+ * A server owns a FIFO of submitted sort requests and a set of admitted
+ * grids that advance together, one iteration per sweep (the kernels of
+ * plas_batch_sort).  A request is admitted as soon as its workspace
+ * (plas_sort_workspace_bytes) fits into 'mem_budget' next to the admitted
+ * ones; requests that arrive while others run join the next sweep.  Results
+ * equal plas_sort of the same request alone (per-grid counters and random
+ * streams).  A server and its calls belong to one host thread.
+ *
+ * plas_server_create: D sort channels for every request; weights: host D
+ *   floats or NULL; sched: host or NULL; mem_budget in bytes (0 = no
+ *   limit); stream: cudaStream_t for all of the server's work.
+ * plas_server_submit: queues *job (copied; the device buffers it names must
+ *   stay valid until the request completes) and returns its ticket (0, 1,
+ *   ...).  PLAS_ERR_BUDGET if the request alone exceeds mem_budget,
+ *   PLAS_ERR_INVALID_ARG for a bad descriptor.
+ * plas_server_step: admits queued requests that fit, runs up to 'sweeps'
+ *   sweeps over the admitted grids, and reports in done[0..*n_done) (at most
+ *   'cap') the tickets whose outputs are complete on return (the call waits
+ *   for the stream).  A finished request's workspace is released before the
+ *   next admission.  job->state_out, if given, is filled on completion.
+ * plas_server_status: queued and admitted requests, device bytes in use.
+ * plas_server_destroy: waits for the stream and frees everything; requests
+ *   still queued or running are abandoned (their outputs are undefined).
+ */
+typedef struct plas_server plas_server;
+int plas_server_create(int D, const float* weights, const plas_schedule* sched,
+                       size_t mem_budget, void* stream, plas_server** out);
+int plas_server_submit(plas_server* srv, const plas_job* job, long long* ticket);
+int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap, int* n_done);
+int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use);
+int plas_server_destroy(plas_server* srv);
 
 /* ---------------------------------------------------------------------- */
 /* diagnostics                                                            */

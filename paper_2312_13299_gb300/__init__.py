@@ -24,7 +24,7 @@ import torch
 from . import _lib
 from ._lib import check, load
 
-__all__ = ["Schedule", "SortResult", "sort", "batch_sort", "gather_rows", "target",
+__all__ = ["Schedule", "SortResult", "sort", "batch_sort", "Server", "gather_rows", "target",
            "group_permutation", "philox", "grid_metrics", "smooth_loss", "SmoothLoss",
            "num_levels", "sort_workspace_bytes", "load"]
 
@@ -36,7 +36,7 @@ class Schedule:
     shrink: float = 0.95
     phi_min: float = 1.0
     tol: float = 1e-4
-    sigma_ratio: float = 0.5
+    sigma_ratio: float = 2.0
     min_block: int = 16
     shuffle_init: bool = True
     normalize: bool = True
@@ -233,6 +233,88 @@ def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] 
     return [SortResult(perm=p, carried=c, state=s.as_dict()) for (p, c), s in zip(outs, states)]
 
 
+class Server:
+    """Continuous batching of sort requests (plas_server_*): requests queue up,
+    are admitted while their workspaces fit the device-memory budget, and
+    advance together one iteration per sweep.  Results equal sort() of each
+    request alone.  All work runs on the stream current at construction."""
+
+    def __init__(self, D: int, weights=None, schedule: Optional[Schedule] = None,
+                 mem_budget: int = 0, device=None):
+        self._lib = load()
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.D = D
+        self._w = _weights(weights, D)
+        self._sched = (schedule or Schedule()).to_c()
+        self._stream = _stream(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.plas_server_create(D, self._w, ctypes.byref(self._sched), mem_budget,
+                                              self._stream, ctypes.byref(h))
+        check(rc, "plas_server_create")
+        self._h = h
+        self._live = {}
+
+    def submit(self, x: torch.Tensor, H: int, W: int, carried: Optional[torch.Tensor] = None,
+               seed: int = 0) -> int:
+        x = _need_cuda(x, "x")
+        if x.shape != (H * W, self.D):
+            raise ValueError("x must be [H*W, D]")
+        perm = torch.empty(H * W, dtype=torch.int32, device=x.device)
+        cout = None
+        if carried is not None:
+            carried = _need_cuda(carried, "carried")
+            cout = torch.empty_like(carried)
+        st = _lib.plas_state()
+        job = _lib.plas_job()
+        job.x, job.H, job.W = x.data_ptr(), H, W
+        job.carried = carried.data_ptr() if carried is not None else None
+        job.C = carried.shape[1] if carried is not None else 0
+        job.seed = seed
+        job.perm_out = perm.data_ptr()
+        job.carried_out = cout.data_ptr() if cout is not None else None
+        job.state_out = ctypes.pointer(st)
+        t = ctypes.c_longlong()
+        with torch.cuda.device(self.device):
+            rc = self._lib.plas_server_submit(self._h, ctypes.byref(job), ctypes.byref(t))
+        check(rc, "plas_server_submit")
+        self._live[t.value] = (x, carried, perm, cout, st)
+        return t.value
+
+    def step(self, sweeps: int = 8) -> list:
+        """Run up to 'sweeps' sweeps; returns [(ticket, SortResult)] of finished requests."""
+        cap = max(1, len(self._live))
+        done = (ctypes.c_longlong * cap)()
+        n = ctypes.c_int()
+        with torch.cuda.device(self.device):
+            rc = self._lib.plas_server_step(self._h, sweeps, done, cap, ctypes.byref(n))
+        check(rc, "plas_server_step")
+        out = []
+        for i in range(n.value):
+            x, car, perm, cout, st = self._live.pop(done[i])
+            out.append((done[i], SortResult(perm=perm, carried=cout, state=st.as_dict())))
+        return out
+
+    def status(self):
+        q, a, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        check(self._lib.plas_server_status(self._h, ctypes.byref(q), ctypes.byref(a),
+                                           ctypes.byref(m)), "plas_server_status")
+        return q.value, a.value, m.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.plas_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def gather_rows(src: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
     """out[p] = src[perm[p]] on the device (every attribute follows the permutation)."""
     src = _need_cuda(src, "src")
@@ -247,7 +329,7 @@ def gather_rows(src: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
 
 
 def target(x: torch.Tensor, H: int, W: int, perm: torch.Tensor, phi: float, weights=None,
-           normalize: bool = True, sigma_ratio: float = 0.5) -> torch.Tensor:
+           normalize: bool = True, sigma_ratio: float = 2.0) -> torch.Tensor:
     """Low-pass target of one arrangement (the blur step of Sec. 3.1) -> [H, W, D]."""
     x = _need_cuda(x, "x")
     perm = _need_cuda(perm, "perm", torch.int32)

@@ -1,0 +1,819 @@
+// engine.cu -- the sweep engine behind plas_sort, plas_batch_sort and the
+// served-sort API (include/plas.h).
+//
+// A sweep advances every admitted grid by one PLAS iteration (Sec. 3.1 of
+// Morgenstern et al., arXiv 2312.13299): grouping table, target pass along y,
+// target pass along x, assignment + schedule step -- one launch per kernel
+// class for all grids.  The schedule runs on the device, so the host only
+// enqueues batches of sweeps and reads each grid's 150-byte state header back
+// once per batch, one batch behind (the GPU never waits for the host inside a
+// level).  A grid whose schedule has ended takes no work in later sweeps; its
+// outputs (permutation, carried attributes) are gathered when the host sees
+// it finished, and its workspace can then be given to a new request.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <vector>
+
+#include "plas_host.h"
+
+namespace plas {
+
+namespace {
+
+enum { kClsGroups = 0, kClsFirY = 1, kClsFirX = 2, kClsAssign = 3, kClsCount = 4 };
+
+struct Job {
+    const float* x = nullptr;
+    int H = 0, W = 0;
+    const float* carried = nullptr;
+    int C = 0;
+    uint64_t seed = 0;
+    const int32_t* perm_init = nullptr;
+    plas_state init{};
+    bool resume = false;
+    int32_t* perm_out = nullptr;
+    float* carried_out = nullptr;
+    float* sorted_out = nullptr;
+    plas_state* state_out = nullptr;
+    long long* trace_S = nullptr;
+    int* trace_level = nullptr;
+    long long trace_cap = 0;
+    long long ticket = 0;
+};
+
+struct Slot {
+    Job job;
+    Geometry geo;
+    Workspace ws{};
+    char* mem = nullptr;
+    size_t bytes = 0;
+    bool owns = false;
+    long long N = 0;
+    int nlev = 0;
+    int ctas[kClsCount] = {0, 0, 0, 0};
+    bool active = false;
+    DevState last{};
+    long long last_it = -1;
+    int stuck = 0;
+};
+
+bool finished(const Slot& s, const plas_schedule& sch) {
+    return s.last.done || s.last.status != 0 || (sch.max_iters > 0 && s.last.it >= sch.max_iters);
+}
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+class Engine {
+   public:
+    Engine(int D, const Weights& w, const plas_schedule& s, cudaStream_t st)
+        : D_(D), w_(w), s_(s), st_(st), nsm_(num_sms()) {}
+    ~Engine() {
+        for (auto& p : marks_) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : pool_) cudaEventDestroy(e);
+        for (auto e : ev_)
+            if (e) cudaEventDestroy(e);
+        if (dmaps_ && dmaps_owned_) cudaFreeAsync(dmaps_, st_);
+    }
+
+    // Multi-grid descriptor arrays come from this arena when given (no
+    // allocation), else from stream-ordered allocations.
+    void set_arena(char* base, size_t bytes) {
+        arena_ = base;
+        arena_bytes_ = bytes;
+    }
+
+    static size_t map_bytes(size_t grids, size_t ctas) {
+        return align_up(grids * sizeof(GridRef), 256) + align_up(ctas * sizeof(CtaMap), 256);
+    }
+
+    int admit(Slot* sl) {
+        const Job& j = sl->job;
+        const int H = j.H, W = j.W;
+        sl->N = (long long)H * W;
+        sl->geo = build_geometry(s_, H, W);
+        sl->nlev = (int)sl->geo.lv.size();
+        workspace_layout(H, W, D_, sl->nlev, sl->geo.table_floats, &sl->ws, sl->mem);
+        DevState init{};
+        if (j.resume) {
+            init.it = j.init.it;
+            init.epoch = j.init.epoch;
+            init.redraws = j.init.redraws;
+            init.level = j.init.level;
+            init.stall = j.init.stall;
+            init.has_prev = j.init.has_prev;
+            init.done = j.init.done;
+            init.d_prev = j.init.d_prev;
+            init.d_last = j.init.d_last;
+        }
+        init.max_iters = s_.max_iters;
+        if (init.level >= sl->nlev) init.done = 1;
+        GridRef ref{};
+        ref.G = sl->ws.G; ref.T = sl->ws.T; ref.H1 = sl->ws.H1; ref.pi = sl->ws.pi;
+        ref.st = sl->ws.st; ref.lv = sl->ws.lv; ref.table = sl->ws.table;
+        ref.H = H; ref.W = W; ref.nlev = sl->nlev; ref.seed = j.seed;
+        ref.trace_S = j.trace_S; ref.trace_level = j.trace_level; ref.trace_cap = j.trace_cap;
+        PLAS_CUDA(cudaMemcpyAsync(sl->ws.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st_));
+        PLAS_CUDA(cudaMemcpyAsync(sl->ws.ref, &ref, sizeof(GridRef), cudaMemcpyHostToDevice, st_));
+        PLAS_CUDA(cudaMemcpyAsync(sl->ws.lv, sl->geo.lv.data(), sizeof(LevelDesc) * sl->nlev,
+                                  cudaMemcpyHostToDevice, st_));
+        PLAS_CUDA(cudaMemcpyAsync(sl->ws.table, sl->geo.table.data(),
+                                  sizeof(float) * sl->geo.table_floats, cudaMemcpyHostToDevice, st_));
+        cudaEvent_t e0 = begin();
+        launch_state_reset(sl->ws.st, st_);
+        launch_minmax(j.x, sl->N, D_, sl->ws.st, nsm_, st_);
+        launch_finalize_prep(sl->ws.st, sl->N, D_, w_, s_.normalize, st_);
+        const int mode = j.perm_init ? 2 : (s_.shuffle_init ? 1 : 0);
+        launch_pack(j.x, (int)sl->N, D_, w_, s_.normalize, sl->ws.st, mode, j.perm_init, j.seed,
+                    sl->ws.G, st_);
+        launch_norms(sl->ws.lv, sl->nlev, H, W, sl->ws.table, st_);
+        end(e0, -1);
+        launches_ += 5;
+        if (int e = check_launch("preparation")) return e;
+        sl->ctas[kClsGroups] = group_ctas(H, W, nsm_);
+        sl->ctas[kClsFirY] = fir_ctas(H, W * D_, kFirLargeRadius);
+        sl->ctas[kClsFirX] = fir_ctas(W, H * D_, kFirLargeRadius);
+        sl->ctas[kClsAssign] = assign_ctas(H, W, nsm_);
+        sl->last = init;
+        sl->active = true;
+        active_.push_back(sl);
+        dirty_ = true;
+        return PLAS_OK;
+    }
+
+    // Enqueue k sweeps over the active grids.
+    int sweeps(int k) {
+        if (active_.empty()) return PLAS_OK;
+        if (dirty_)
+            if (int e = rebuild()) return e;
+        const bool one = active_.size() == 1;
+        const GridRef* grids = one ? active_[0]->ws.ref : dgrids_;
+        // FIR tiling: one grid follows the radius it last reported (both tilings
+        // give the same bits; a stale choice only costs time); many grids use
+        // the large-radius tiling their CTA maps were built for
+        int var = kFirLargeRadius;
+        int fir_ctas_one[2] = {0, 0};
+        if (one) {
+            const Slot* sl = active_[0];
+            const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
+            var = sl->geo.lv[L].r < kFirSmallRadiusLimit ? kFirSmallRadius : kFirLargeRadius;
+            fir_ctas_one[0] = fir_ctas(sl->job.H, sl->job.W * D_, var);
+            fir_ctas_one[1] = fir_ctas(sl->job.W, sl->job.H * D_, var);
+        }
+        for (int i = 0; i < k; ++i) {
+            for (int c = 0; c < kClsCount; ++c) {
+                const CtaMap* map = one ? nullptr : dmap_[c];
+                int ctas = one ? active_[0]->ctas[c] : total_[c];
+                if (one && c == kClsFirY) ctas = fir_ctas_one[0];
+                if (one && c == kClsFirX) ctas = fir_ctas_one[1];
+                cudaEvent_t e0 = begin();
+                switch (c) {
+                    case kClsGroups: launch_group_table(grids, map, ctas, st_); break;
+                    case kClsFirY: launch_fir(0, grids, map, ctas, D_, var, st_); break;
+                    case kClsFirX: launch_fir(1, grids, map, ctas, D_, var, st_); break;
+                    default: launch_assign(grids, map, ctas, D_, s_.tol, st_); break;
+                }
+                end(e0, c);
+            }
+            launches_ += kClsCount;
+        }
+        return check_launch("sweep");
+    }
+
+    // Enqueue a read-back of every active grid's state header into host
+    // buffer 'buf' (0 or 1) and record its event.
+    int poll(int buf) {
+        const size_t hb = kStateHeaderBytes;
+        if (active_.size() > host_cap_ || host_ == nullptr) {
+            // a grown buffer replaces the old one, which stays allocated, so
+            // a read-back still in flight keeps a valid destination
+            host_cap_ = std::max<size_t>({active_.size(), 2 * host_cap_, 8});
+            if (int e = host_buffers(2 * host_cap_ * hb)) return e;
+        }
+        polled_[buf] = active_;
+        polled_base_[buf] = host_ + buf * host_cap_ * hb;
+        for (size_t i = 0; i < active_.size(); ++i)
+            PLAS_CUDA(cudaMemcpyAsync(polled_base_[buf] + i * hb, active_[i]->ws.st, hb,
+                                      cudaMemcpyDeviceToHost, st_));
+        PLAS_CUDA(cudaEventRecord(ev_[buf], st_));
+        return PLAS_OK;
+    }
+
+    // Wait for poll 'buf' and store each polled grid's state.
+    int wait(int buf) {
+        PLAS_CUDA(cudaEventSynchronize(ev_[buf]));
+        const size_t hb = kStateHeaderBytes;
+        for (size_t i = 0; i < polled_[buf].size(); ++i) {
+            Slot* sl = polled_[buf][i];
+            memcpy(&sl->last, polled_base_[buf] + i * hb, hb);
+            if (!finished(*sl, s_)) {
+                sl->stuck = (sl->last.it == sl->last_it) ? sl->stuck + 1 : 0;
+                sl->last_it = sl->last.it;
+                if (sl->stuck > 4)
+                    return fail(PLAS_ERR_INTERNAL, "grid made no progress at iteration %lld", sl->last.it);
+            }
+        }
+        return PLAS_OK;
+    }
+
+    // Enqueue the outputs of a finished grid and take it out of the sweeps.
+    int retire(Slot* sl) {
+        const Job& j = sl->job;
+        if (sl->last.status == 0) {
+            launch_extract_perm(sl->ws.G, (int)sl->N, D_, j.perm_out, st_);
+            launches_ += 1;
+            if (j.carried && j.carried_out && j.C > 0) {
+                launch_gather_rows(j.carried, sl->N, j.C, j.perm_out, j.carried_out, st_);
+                launches_ += 1;
+            }
+            if (j.sorted_out) {
+                launch_gather_rows(j.x, sl->N, D_, j.perm_out, j.sorted_out, st_);
+                launches_ += 1;
+            }
+        }
+        sl->active = false;
+        active_.erase(std::find(active_.begin(), active_.end(), sl));
+        dirty_ = true;
+        return check_launch("outputs");
+    }
+
+    // Per-class event times (call after the stream is synchronised).
+    void harvest() {
+        for (auto& m : marks_) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, m.a, m.b);
+            const int k = m.cls < 0 ? PLAS_K_PREP : class_to_stat(m.cls);
+            ks_[k].launches += (m.cls < 0) ? 5 : 1;
+            ks_[k].ms += ms;
+            pool_.push_back(m.a);
+            pool_.push_back(m.b);
+        }
+        marks_.clear();
+    }
+
+    static int class_to_stat(int c) {
+        switch (c) {
+            case kClsGroups: return PLAS_K_GROUPS;
+            case kClsFirY: return PLAS_K_BLUR_COLS;
+            case kClsFirX: return PLAS_K_BLUR_ROWS;
+            default: return PLAS_K_ASSIGN;
+        }
+    }
+
+    std::vector<Slot*>& active() { return active_; }
+    plas_kernel_stat ks_[PLAS_K_COUNT] = {};
+    long long launches_ = 0;
+
+   private:
+    cudaEvent_t begin() {
+        if (!s_.profile) return nullptr;
+        cudaEvent_t e = get_event();
+        cudaEventRecord(e, st_);
+        return e;
+    }
+    void end(cudaEvent_t a, int cls) {
+        if (!s_.profile || !a) return;
+        cudaEvent_t b = get_event();
+        cudaEventRecord(b, st_);
+        marks_.push_back({a, b, cls});
+    }
+    cudaEvent_t get_event() {
+        if (!pool_.empty()) {
+            cudaEvent_t e = pool_.back();
+            pool_.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+
+    int host_buffers(size_t bytes) {
+        void* h = nullptr;
+        cudaEvent_t unused[2];
+        if (int e = poll_buffers(bytes, &h, unused)) return e;
+        host_ = (char*)h;
+        if (!ev_[0]) {
+            PLAS_CUDA(cudaEventCreateWithFlags(&ev_[0], cudaEventDisableTiming));
+            PLAS_CUDA(cudaEventCreateWithFlags(&ev_[1], cudaEventDisableTiming));
+        }
+        return PLAS_OK;
+    }
+
+    // Descriptor array and CTA maps of the active grids (multi-grid sweeps).
+    int rebuild() {
+        dirty_ = false;
+        if (active_.size() <= 1) return PLAS_OK;
+        std::vector<GridRef> refs(active_.size());
+        for (size_t i = 0; i < active_.size(); ++i) {
+            Slot* sl = active_[i];
+            GridRef& r = refs[i];
+            r.G = sl->ws.G; r.T = sl->ws.T; r.H1 = sl->ws.H1; r.pi = sl->ws.pi; r.st = sl->ws.st;
+            r.lv = sl->ws.lv; r.table = sl->ws.table; r.H = sl->job.H; r.W = sl->job.W;
+            r.nlev = sl->nlev; r.seed = sl->job.seed;
+            r.trace_S = sl->job.trace_S; r.trace_level = sl->job.trace_level;
+            r.trace_cap = sl->job.trace_cap;
+        }
+        std::vector<CtaMap> maps;
+        for (int c = 0; c < kClsCount; ++c) {
+            total_[c] = 0;
+            for (size_t i = 0; i < active_.size(); ++i) {
+                const int n = active_[i]->ctas[c];
+                for (int l = 0; l < n; ++l) maps.push_back(CtaMap{(int)i, l, n, 0});
+                total_[c] += n;
+            }
+        }
+        const size_t need = map_bytes(refs.size(), maps.size());
+        if (need > dmaps_cap_) {
+            if (arena_) {
+                if (need > arena_bytes_) return fail(PLAS_ERR_INTERNAL, "descriptor arena too small");
+                dmaps_ = arena_;
+                dmaps_cap_ = arena_bytes_;
+            } else {
+                if (dmaps_ && dmaps_owned_) cudaFreeAsync(dmaps_, st_);  // stream-ordered
+                void* p = nullptr;
+                if (cudaMallocAsync(&p, need * 2, st_) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(PLAS_ERR_OOM, "descriptor allocation failed");
+                }
+                dmaps_ = (char*)p;
+                dmaps_cap_ = need * 2;
+                dmaps_owned_ = true;
+            }
+        }
+        dgrids_ = (GridRef*)dmaps_;
+        CtaMap* m = (CtaMap*)(dmaps_ + align_up(refs.size() * sizeof(GridRef), 256));
+        size_t o = 0;
+        for (int c = 0; c < kClsCount; ++c) {
+            dmap_[c] = m + o;
+            o += total_[c];
+        }
+        // Stream-ordered: sweeps already enqueued read the arrays before the
+        // copies land.  The sources are pageable, so each copy is staged before
+        // the call returns and the vectors may go out of scope.
+        PLAS_CUDA(cudaMemcpyAsync(dgrids_, refs.data(), refs.size() * sizeof(GridRef),
+                                  cudaMemcpyHostToDevice, st_));
+        PLAS_CUDA(cudaMemcpyAsync(m, maps.data(), maps.size() * sizeof(CtaMap),
+                                  cudaMemcpyHostToDevice, st_));
+        return PLAS_OK;
+    }
+
+    int D_;
+    Weights w_;
+    plas_schedule s_;
+    cudaStream_t st_;
+    int nsm_;
+    std::vector<Slot*> active_;
+    std::vector<Slot*> polled_[2];
+    bool dirty_ = true;
+    char* arena_ = nullptr;
+    size_t arena_bytes_ = 0;
+    char* dmaps_ = nullptr;
+    size_t dmaps_cap_ = 0;
+    bool dmaps_owned_ = false;
+    GridRef* dgrids_ = nullptr;
+    CtaMap* dmap_[kClsCount] = {nullptr, nullptr, nullptr, nullptr};
+    int total_[kClsCount] = {0, 0, 0, 0};
+    char* host_ = nullptr;
+    size_t host_cap_ = 0;
+    char* polled_base_[2] = {nullptr, nullptr};
+    cudaEvent_t ev_[2] = {nullptr, nullptr};
+    std::vector<EventPair> marks_;
+    std::vector<cudaEvent_t> pool_;
+};
+
+int status_error(const DevState& st) {
+    if (st.nonfinite) return fail(PLAS_ERR_NONFINITE, "sort input holds NaN or Inf");
+    if (st.bad_index) return fail(PLAS_ERR_INVALID_ARG, "perm_init holds an index outside [0, N)");
+    return fail(PLAS_ERR_INTERNAL, "device status %d", st.status);
+}
+
+void to_public(const DevState& d, plas_state* o) {
+    o->it = d.it;
+    o->epoch = d.epoch;
+    o->redraws = d.redraws;
+    o->level = d.level;
+    o->stall = d.stall;
+    o->has_prev = d.has_prev;
+    o->done = d.done;
+    o->d_prev = d.d_prev;
+    o->d_last = d.d_last;
+    o->scale_exp = d.scale_exp;
+    o->status = d.status;
+}
+
+int check_job(const plas_job& j, int D, int* skip) {
+    *skip = 0;
+    if (j.H < 0 || j.W < 0) return fail(PLAS_ERR_INVALID_ARG, "grid sides must be >= 0");
+    const long long N = (long long)j.H * j.W;
+    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    if (N == 0) {
+        *skip = 1;
+        return PLAS_OK;
+    }
+    if (!j.x || !j.perm_out) return fail(PLAS_ERR_INVALID_ARG, "job needs x and perm_out");
+    if (!aligned(j.x, 4) || !aligned(j.perm_out, 4)) return fail(PLAS_ERR_INVALID_ARG, "misaligned pointer");
+    if (j.C < 0 || (j.C > 0 && (!j.carried || !j.carried_out)))
+        return fail(PLAS_ERR_INVALID_ARG, "carried/carried_out required when C > 0");
+    (void)D;
+    return PLAS_OK;
+}
+
+Job job_from(const plas_job& j) {
+    Job o;
+    o.x = j.x; o.H = j.H; o.W = j.W; o.carried = j.carried; o.C = j.C; o.seed = j.seed;
+    o.perm_out = j.perm_out; o.carried_out = j.carried_out; o.state_out = j.state_out;
+    return o;
+}
+
+int make_weights(const float* weights, int D, Weights* w) {
+    for (int d = 0; d < kMaxD; ++d) w->w[d] = (d < D) ? (weights ? weights[d] : 1.0f) : 0.0f;
+    for (int d = 0; d < D; ++d)
+        if (!std::isfinite(w->w[d])) return fail(PLAS_ERR_INVALID_ARG, "weights must be finite");
+    return PLAS_OK;
+}
+
+// Run every admitted grid of 'eng' to completion (batches of k sweeps, one
+// batch of look-ahead), retiring grids as they finish.
+int run_all(Engine& eng, const plas_schedule& s) {
+    const int k = s.iters_per_poll > 0 ? s.iters_per_poll : 8;
+    int buf = 0;
+    bool pending = false;
+    int first_error = PLAS_OK;
+    // grids that are finished before the first sweep (e.g. resumed at the end)
+    for (auto* sl : std::vector<Slot*>(eng.active()))
+        if (finished(*sl, s)) {
+            if (sl->last.status && !first_error) first_error = status_error(sl->last);
+            if (int e = eng.retire(sl)) return e;
+        }
+    while (!eng.active().empty()) {
+        if (int e = eng.sweeps(k)) return e;
+        if (int e = eng.poll(buf)) return e;
+        if (pending) {
+            if (int e = eng.wait(buf ^ 1)) return e;
+            for (auto* sl : std::vector<Slot*>(eng.active()))
+                if (finished(*sl, s)) {
+                    if (sl->last.status && !first_error) first_error = status_error(sl->last);
+                    if (int e = eng.retire(sl)) return e;
+                }
+        }
+        pending = true;
+        buf ^= 1;
+    }
+    if (pending)
+        if (int e = eng.wait(buf ^ 1)) return e;  // the last poll
+    return first_error;
+}
+
+}  // namespace
+
+}  // namespace plas
+
+using namespace plas;
+
+// ===========================================================================
+// the sort
+// ===========================================================================
+extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weights,
+                         const float* carried, int C, uint64_t seed, const plas_schedule* sched,
+                         const int32_t* perm_init, plas_state* state_io, int32_t* perm_out,
+                         float* carried_out, float* sorted_out, void* workspace, size_t ws_bytes,
+                         plas_stats* stats, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    set_last_error("");
+    if (H < 0 || W < 0) return fail(PLAS_ERR_INVALID_ARG, "grid sides must be >= 0");
+    if (!channels_supported(D))
+        return fail(PLAS_ERR_INVALID_ARG, "D=%d not supported (1..16, 20, 24, 32, 48, 64)", D);
+    const long long N = (long long)H * W;
+    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    if (C < 0 || (C > 0 && (!carried || !carried_out)))
+        return fail(PLAS_ERR_INVALID_ARG, "carried/carried_out required when C > 0");
+    plas_schedule s;
+    if (sched) s = *sched; else plas_default_schedule(&s);
+    if (int e = validate_schedule(s)) return e;
+    if (N == 0) {
+        if (state_io) { memset(state_io, 0, sizeof(*state_io)); state_io->done = 1; }
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return PLAS_OK;
+    }
+    if (!x || !perm_out) return fail(PLAS_ERR_INVALID_ARG, "x and perm_out are required");
+    if (!aligned(x, 4) || !aligned(perm_out, 4)) return fail(PLAS_ERR_INVALID_ARG, "misaligned pointer");
+    const bool resume = state_io && (state_io->it > 0 || state_io->level > 0);
+    if (resume && !perm_init) return fail(PLAS_ERR_INVALID_ARG, "resuming needs perm_init");
+    if (resume && (state_io->level < 0 || state_io->it < 0))
+        return fail(PLAS_ERR_INVALID_ARG, "invalid resume state");
+    Weights w{};
+    if (int e = make_weights(weights, D, &w)) return e;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    Slot sl;
+    Job& j = sl.job;
+    j.x = x; j.H = H; j.W = W; j.carried = carried; j.C = C; j.seed = seed;
+    j.perm_init = perm_init; j.resume = resume;
+    if (resume) j.init = *state_io;
+    j.perm_out = perm_out; j.carried_out = carried_out; j.sorted_out = sorted_out;
+    j.trace_S = s.trace_S; j.trace_level = s.trace_level; j.trace_cap = s.trace_cap;
+
+    const size_t need = sort_workspace_bytes(H, W, D, s);
+    if (workspace) {
+        if (ws_bytes < need) return fail(PLAS_ERR_INVALID_ARG, "workspace too small (%zu < %zu)", ws_bytes, need);
+        if (!aligned(workspace, 256)) return fail(PLAS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        sl.mem = (char*)workspace;
+    } else {
+        void* mem = nullptr;
+        if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PLAS_ERR_OOM, "workspace allocation of %zu bytes failed", need);
+        }
+        sl.mem = (char*)mem;
+        sl.owns = true;
+    }
+    int rc = PLAS_OK;
+    {
+        Engine eng(D, w, s, st);
+        rc = eng.admit(&sl);
+        if (rc == PLAS_OK) rc = run_all(eng, s);
+        if (rc == PLAS_OK && stats) {
+            memset(stats, 0, sizeof(*stats));
+            double macc[4] = {0, 0, 0, 0};
+            if (cudaMemsetAsync(sl.ws.macc, 0, sizeof(double) * 4, st) != cudaSuccess) rc = fail(PLAS_ERR_CUDA, "memset failed");
+            launch_neighbour_metrics(sl.ws.G, grid_stride(D), H, W, D, 1.0, sl.ws.macc, num_sms(), st);
+            eng.launches_ += 1;
+            DevState fin{};
+            if (rc == PLAS_OK &&
+                (cudaMemcpyAsync(macc, sl.ws.macc, sizeof(double) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                 cudaMemcpyAsync(&fin, sl.ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                 cudaStreamSynchronize(st) != cudaSuccess))
+                rc = fail(PLAS_ERR_CUDA, "stats readback failed");
+            if (rc == PLAS_OK) {
+                eng.harvest();
+                const long long npairs = (long long)H * (W - 1) + (long long)(H - 1) * W;
+                stats->iterations = fin.it;
+                stats->redraws = fin.redraws;
+                stats->grouped_cells = fin.grouped;
+                stats->levels = sl.nlev;
+                stats->status = fin.status;
+                stats->final_l2_to_target = fin.d_last;
+                stats->neighbour_l2 = npairs > 0 ? macc[0] / (double)npairs : 0.0;
+                for (int c = 0; c < PLAS_K_COUNT; ++c) stats->kernel[c] = eng.ks_[c];
+                const double its = (double)(fin.it - (resume ? state_io->it : 0));
+                stats->kernel[PLAS_K_PREP].bytes = (double)N * D * 8 + (double)N * grid_stride(D) * 4;
+                stats->kernel[PLAS_K_BLUR_COLS].bytes = its * 8.0 * (double)N * D;
+                stats->kernel[PLAS_K_BLUR_COLS].flops = 2.0 * fin.fmas_y;
+                stats->kernel[PLAS_K_BLUR_ROWS].bytes = its * 8.0 * (double)N * D;
+                stats->kernel[PLAS_K_BLUR_ROWS].flops = 2.0 * fin.fmas_x;
+                stats->kernel[PLAS_K_GROUPS].bytes = 4.0 * fin.beta2_sum;
+                stats->kernel[PLAS_K_ASSIGN].bytes =
+                    (double)fin.grouped * (12.0 * D + 8.0) + (its * N - (double)fin.grouped) * 8.0 * D;
+                stats->kernel[PLAS_K_GATHER].bytes = (double)N * 8 + (carried_out ? (double)N * C * 8 : 0.0) +
+                                                     (sorted_out ? (double)N * D * 8 : 0.0);
+                stats->launches = eng.launches_;
+            }
+        } else if (rc == PLAS_OK) {
+            if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PLAS_ERR_CUDA, "stream sync failed");
+        }
+        if (rc == PLAS_OK && state_io) to_public(sl.last, state_io);
+        if (rc != PLAS_OK && state_io && sl.last.status) to_public(sl.last, state_io);
+    }
+    if (sl.owns) cudaFreeAsync(sl.mem, st);
+    if (stats && rc == PLAS_OK)
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+// ===========================================================================
+// batched sort
+// ===========================================================================
+static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedule& s,
+                          std::vector<size_t>* per_job, size_t* maps_at) {
+    size_t total = 0, grids = 0, ctas = 0;
+    const int nsm = num_sms();
+    if (per_job) per_job->assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const int H = jobs[i].H, W = jobs[i].W;
+        if (H < 1 || W < 1) continue;
+        const size_t b = align_up(sort_workspace_bytes(H, W, D, s), 256);
+        if (per_job) (*per_job)[i] = b;
+        total += b;
+        grids += 1;
+        ctas += group_ctas(H, W, nsm) + fir_ctas(H, W * D, kFirLargeRadius) +
+                fir_ctas(W, H * D, kFirLargeRadius) + assign_ctas(H, W, nsm);
+    }
+    if (maps_at) *maps_at = total;
+    return total + Engine::map_bytes(grids, ctas);
+}
+
+extern "C" size_t plas_batch_workspace_bytes(int n, const plas_job* jobs, int D) {
+    if (n < 0 || (n > 0 && !jobs) || !channels_supported(D)) return 0;
+    plas_schedule s;
+    plas_default_schedule(&s);
+    return batch_bytes(n, jobs, D, s, nullptr, nullptr);
+}
+
+extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
+                               const plas_schedule* sched, void* workspace, size_t ws_bytes,
+                               void* stream) {
+    set_last_error("");
+    if (n < 0 || (n > 0 && !jobs)) return fail(PLAS_ERR_INVALID_ARG, "bad job list");
+    if (!channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "D=%d not supported", D);
+    plas_schedule s;
+    if (sched) s = *sched; else plas_default_schedule(&s);
+    s.trace_S = nullptr;  // traces are a single-sort facility
+    s.trace_level = nullptr;
+    s.trace_cap = 0;
+    if (int e = validate_schedule(s)) return e;
+    Weights w{};
+    if (int e = make_weights(weights, D, &w)) return e;
+    for (int i = 0; i < n; ++i) {
+        int skip = 0;
+        if (int e = check_job(jobs[i], D, &skip)) return e;
+        if (skip && jobs[i].state_out) {
+            memset(jobs[i].state_out, 0, sizeof(plas_state));
+            jobs[i].state_out->done = 1;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<size_t> per;
+    size_t maps_at = 0;
+    const size_t need = batch_bytes(n, jobs, D, s, &per, &maps_at);
+    char* base = nullptr;
+    bool owns = false;
+    if (workspace) {
+        if (ws_bytes < need) return fail(PLAS_ERR_INVALID_ARG, "batch workspace too small (%zu < %zu)", ws_bytes, need);
+        if (!aligned(workspace, 256)) return fail(PLAS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        base = (char*)workspace;
+    } else {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PLAS_ERR_OOM, "batch workspace allocation of %zu bytes failed", need);
+        }
+        base = (char*)p;
+        owns = true;
+    }
+    int rc = PLAS_OK;
+    {
+        std::vector<std::unique_ptr<Slot>> slots;
+        Engine eng(D, w, s, st);
+        eng.set_arena(base + maps_at, need - maps_at);
+        size_t off = 0;
+        for (int i = 0; i < n && rc == PLAS_OK; ++i) {
+            if (per[i] == 0) continue;
+            auto sl = std::make_unique<Slot>();
+            sl->job = job_from(jobs[i]);
+            sl->mem = base + off;
+            off += per[i];
+            rc = eng.admit(sl.get());
+            slots.push_back(std::move(sl));
+        }
+        if (rc == PLAS_OK) rc = run_all(eng, s);
+        if (rc == PLAS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PLAS_ERR_CUDA, "stream sync failed");
+        if (rc == PLAS_OK)
+            for (auto& sl : slots)
+                if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
+    }
+    if (owns) cudaFreeAsync(base, st);
+    return rc;
+}
+
+// ===========================================================================
+// served sorts (continuous batching)
+// ===========================================================================
+struct plas_server {
+    int D = 0;
+    Weights w{};
+    plas_schedule s{};
+    size_t budget = 0;
+    size_t in_use = 0;
+    cudaStream_t st = nullptr;
+    std::unique_ptr<Engine> eng;
+    std::deque<std::unique_ptr<Slot>> queue;
+    std::vector<std::unique_ptr<Slot>> running;
+    std::vector<long long> completed;  // finished, not yet reported
+    long long next_ticket = 0;
+};
+
+extern "C" int plas_server_create(int D, const float* weights, const plas_schedule* sched,
+                                  size_t mem_budget, void* stream, plas_server** out) {
+    set_last_error("");
+    if (!out) return fail(PLAS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "D=%d not supported", D);
+    auto srv = std::make_unique<plas_server>();
+    srv->D = D;
+    if (int e = make_weights(weights, D, &srv->w)) return e;
+    if (sched) srv->s = *sched; else plas_default_schedule(&srv->s);
+    srv->s.trace_S = nullptr;
+    srv->s.trace_level = nullptr;
+    srv->s.trace_cap = 0;
+    if (int e = validate_schedule(srv->s)) return e;
+    srv->budget = mem_budget;
+    srv->st = (cudaStream_t)stream;
+    srv->eng = std::make_unique<Engine>(D, srv->w, srv->s, srv->st);
+    *out = srv.release();
+    return PLAS_OK;
+}
+
+extern "C" int plas_server_submit(plas_server* srv, const plas_job* job, long long* ticket) {
+    set_last_error("");
+    if (!srv || !job) return fail(PLAS_ERR_INVALID_ARG, "NULL server or job");
+    int skip = 0;
+    if (int e = check_job(*job, srv->D, &skip)) return e;
+    auto sl = std::make_unique<Slot>();
+    sl->job = job_from(*job);
+    sl->job.ticket = srv->next_ticket++;
+    if (ticket) *ticket = sl->job.ticket;
+    if (skip) {
+        if (job->state_out) {
+            memset(job->state_out, 0, sizeof(plas_state));
+            job->state_out->done = 1;
+        }
+        srv->completed.push_back(sl->job.ticket);
+        return PLAS_OK;
+    }
+    sl->bytes = align_up(sort_workspace_bytes(job->H, job->W, srv->D, srv->s), 256);
+    if (srv->budget && sl->bytes > srv->budget)
+        return fail(PLAS_ERR_BUDGET, "request needs %zu bytes, budget is %zu", sl->bytes, srv->budget);
+    srv->queue.push_back(std::move(sl));
+    return PLAS_OK;
+}
+
+extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap,
+                                int* n_done) {
+    set_last_error("");
+    if (!srv || !n_done || sweeps < 0 || cap < 0 || (cap > 0 && !done))
+        return fail(PLAS_ERR_INVALID_ARG, "bad arguments");
+    *n_done = 0;
+    // admission: FIFO, while the next request fits the budget
+    while (!srv->queue.empty()) {
+        Slot* sl = srv->queue.front().get();
+        if (srv->budget && srv->in_use + sl->bytes > srv->budget) break;
+        void* mem = nullptr;
+        if (cudaMallocAsync(&mem, sl->bytes, srv->st) != cudaSuccess) {
+            cudaGetLastError();
+            if (srv->running.empty()) return fail(PLAS_ERR_OOM, "workspace allocation failed");
+            break;  // wait for running requests to release memory
+        }
+        sl->mem = (char*)mem;
+        sl->owns = true;
+        srv->in_use += sl->bytes;
+        if (int e = srv->eng->admit(sl)) return e;
+        srv->running.push_back(std::move(srv->queue.front()));
+        srv->queue.pop_front();
+    }
+    if (!srv->running.empty()) {
+        // grids that ended before this step's sweeps need no further work
+        if (int e = srv->eng->sweeps(sweeps > 0 ? sweeps : 1)) return e;
+        if (int e = srv->eng->poll(0)) return e;
+        if (int e = srv->eng->wait(0)) return e;
+        std::vector<Slot*> fin;
+        for (auto* sl : std::vector<Slot*>(srv->eng->active()))
+            if (finished(*sl, srv->s)) {
+                if (int e = srv->eng->retire(sl)) return e;
+                fin.push_back(sl);
+            }
+        if (!fin.empty()) {
+            PLAS_CUDA(cudaStreamSynchronize(srv->st));  // outputs complete
+            for (Slot* sl : fin) {
+                if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
+                srv->completed.push_back(sl->job.ticket);
+                cudaFreeAsync(sl->mem, srv->st);
+                srv->in_use -= sl->bytes;
+                srv->running.erase(std::find_if(srv->running.begin(), srv->running.end(),
+                                                [sl](const std::unique_ptr<Slot>& p) { return p.get() == sl; }));
+            }
+        }
+    }
+    const int n = std::min<int>(cap, (int)srv->completed.size());
+    for (int i = 0; i < n; ++i) done[i] = srv->completed[i];
+    srv->completed.erase(srv->completed.begin(), srv->completed.begin() + n);
+    *n_done = n;
+    return PLAS_OK;
+}
+
+extern "C" int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use) {
+    if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
+    if (queued) *queued = (int)srv->queue.size();
+    if (active) *active = (int)srv->running.size();
+    if (mem_in_use) *mem_in_use = srv->in_use;
+    return PLAS_OK;
+}
+
+extern "C" int plas_server_destroy(plas_server* srv) {
+    if (!srv) return PLAS_OK;
+    cudaStreamSynchronize(srv->st);
+    for (auto& sl : srv->running)
+        if (sl->owns) cudaFreeAsync(sl->mem, srv->st);
+    srv->eng.reset();
+    cudaStreamSynchronize(srv->st);
+    delete srv;
+    return PLAS_OK;
+}

@@ -1,0 +1,263 @@
+// fir_kernels.cu -- the low-pass target of the PLAS sort (Sec. 3.1 of
+// Morgenstern et al., arXiv 2312.13299: the grid is low-pass filtered into an
+// idealised target whose kernel shrinks with the radius), one separable pass
+// per launch, over every grid of a sweep.
+//
+// A pass filters the columns of a logical R x NC matrix along its rows (the
+// blur axis).  Pass 0 runs along y on the working grid (columns = (x, d);
+// output written as [x][y][d]); pass 1 runs along x on that output (columns =
+// (y, d); output = the target [y][x][d]).
+//
+// A CTA owns 128 columns and TY output rows (128 or 32, see FirTiling).  Lane l handles the four
+// columns c0+l, c0+32+l, c0+64+l, c0+96+l as two packed pairs, so each tap step
+// is 16 fma.rn.f32x2 (two independent IEEE round-to-nearest FMAs each) fed by
+// one 16-byte shared-memory load; warp q owns output rows 8q..8q+7 and keeps
+// them in registers.  Input rows stream through a ring in shared memory
+// ([row][lane][4 columns]) in chunks of tap steps: cp.async fetches
+// the next chunk's rows and taps while the current one is computed, and
+// out-of-grid rows are zero-filled by the copy.  Each output is the ascending-tap FMA chain
+// over the zero-padded column: a zero tap or a zero sample leaves the chain
+// bit-for-bit unchanged (the accumulator starts at +0 and never becomes -0),
+// so padded and per-warp trimmed step ranges give exactly the in-range sum.
+// It is then divided by the in-range tap mass.
+#include <algorithm>
+
+#include "plas_kernels.h"
+
+namespace plas {
+
+static_assert(kFirCols == 128, "four columns per lane");
+
+// Two tilings of the same kernel (identical results): rows per CTA, ring rows,
+// tap steps per chunk.  The large one keeps 16 warps per CTA busy at large
+// radii; the small one (4 CTAs per SM) overlaps the short load / compute /
+// store phases of small radii across CTAs.
+template <int TY_, int RING_, int CH_, int MINB_>
+struct FirTiling {
+    static constexpr int TY = TY_, RING = RING_, CH = CH_, MINB = MINB_;
+    static constexpr int THREADS = 32 * TY / kFirX;
+    static_assert(RING >= 2 * CH + TY + kFirX, "ring must hold two chunks + span");
+    static_assert((RING & (RING - 1)) == 0 && CH % kFirX == 0, "ring power of two, chunk of 8s");
+};
+using FirLarge = FirTiling<128, 256, 56, 1>;
+using FirSmall = FirTiling<32, 64, 8, 4>;
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ void cp_async_f32(float* sdst, const float* gsrc, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <class TL>
+__global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
+    int pass, const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, int D, int gs,
+    int ts) {
+    constexpr int X = kFirX;
+    constexpr int kFirTY = TL::TY, kFirRing = TL::RING, kFirChunk = TL::CH;
+    constexpr int kFirThreads = TL::THREADS;
+    constexpr int RM = kFirRing - 1;
+    constexpr int NW = kFirThreads / 32;
+    const CtaRef cr = resolve_cta(map);
+    const GridRef& gr = grids[cr.g];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const LevelDesc& lv = gr.lv[st->level];
+
+    const float* in;
+    long long in_row, in_cell;
+    int R, NC, r, rp, ntp;
+    const float* taps;
+    if (pass == 0) {  // along y: G -> H1 ([x][y][d])
+        in = gr.G; in_row = (long long)gr.W * gs; in_cell = gs;
+        R = gr.H; NC = gr.W * D;
+        r = lv.ry; rp = lv.rpy; ntp = lv.ntpy;
+        taps = gr.table + lv.off_ty;
+    } else {          // along x: H1 -> T ([y][x][d], cell stride ts)
+        in = gr.H1; in_row = (long long)gr.H * D; in_cell = D;
+        R = gr.W; NC = gr.H * D;
+        r = lv.rx; rp = lv.rpx; ntp = lv.ntpx;
+        taps = gr.table + lv.off_tx;
+    }
+    const int ncol = (NC + kFirCols - 1) / kFirCols;
+    const int c0 = (cr.local % ncol) * kFirCols;
+    const int t0 = (cr.local / ncol) * kFirTY;
+
+    extern __shared__ __align__(16) ulonglong2 ring[];  // kFirRing x 32 lanes x 4 columns
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    long long inoff[4];
+    bool ok[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = c0 + 32 * k + lane;
+        ok[k] = c < NC;
+        inoff[k] = ok[k] ? (long long)(c / D) * in_cell + c % D : 0;
+    }
+
+    // CTA step range: non-zero taps that reach an in-range row for some output
+    int jlo = max(rp - r, rp - (t0 + kFirTY - 1));
+    jlo = jlo / X * X;
+    const int jhi = min(rp + r, rp + R - 1 - t0);
+    const int jend = min(ntp, (jhi + X) / X * X);
+    // warp step range: the same for this warp's 8 output rows
+    const int rbase = q * X;
+    const int ylo = t0 + rbase;
+    const bool wact = ylo < R;
+    const int yhi = min(ylo + X, R) - 1;
+    int wlo = max(rp - r, rp - yhi);
+    wlo = max(jlo, wlo / X * X);
+    const int whi = min(rp + r, rp + R - 1 - ylo);
+    const int wend = min(jend, (whi + X) / X * X);
+
+    const int span = kFirTY + X;  // rows read past the last step of a chunk
+    auto fetch = [&](int t) {
+        const int yy = t0 - rp + t;
+        const bool rowok = yy >= 0 && yy < R;
+        float* dst = reinterpret_cast<float*>(ring + (t & RM) * 32 + lane);
+        const float* base = in + (rowok ? (long long)yy * in_row : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cp_async_f32(dst + k, base + inoff[k], rowok && ok[k]);
+    };
+    // taps of a chunk, (k, k) pairs, double-buffered next to the ring
+    __shared__ __align__(16) unsigned long long tapbuf[2][kFirChunk];
+    const unsigned long long* tp = reinterpret_cast<const unsigned long long*>(taps);
+    auto fetch_taps = [&](int from, int to, int b) {  // steps [from, to), multiples of 8
+        for (int p = threadIdx.x; 2 * p < to - from; p += kFirThreads)
+            cp_async_16(&tapbuf[b][2 * p], tp + from + 2 * p);
+    };
+    int loaded_end = min(jlo + kFirChunk, jend) + span;
+    fetch_taps(jlo, min(jlo + kFirChunk, jend), 0);
+    for (int t = jlo + q; t < loaded_end; t += NW) fetch(t);
+    cp_async_wait_all();
+    __syncthreads();
+
+    ulonglong2 acc[X], win[X];
+#pragma unroll
+    for (int i = 0; i < X; ++i) acc[i] = make_ulonglong2(0ull, 0ull);
+    bool started = false;
+    int ci = 0;
+    for (int jc = jlo; jc < jend; jc += kFirChunk, ++ci) {
+        const int cend = min(jc + kFirChunk, jend);
+        // the ring holds >= 2 chunks + kFirTY + X rows, so the next chunk's rows
+        // never land on a row that the current chunk still reads; the other tap
+        // buffer was last read by the previous chunk, before its barrier
+        const int next_end = min(cend + kFirChunk, jend) + span;
+        if (cend < jend) fetch_taps(cend, min(cend + kFirChunk, jend), (ci + 1) & 1);
+        for (int t = loaded_end + q; t < next_end; t += NW) fetch(t);
+        loaded_end = max(loaded_end, next_end);
+        const unsigned long long* tb = tapbuf[ci & 1];
+        if (wact) {
+            const int s0 = max(jc, wlo), s1 = min(cend, wend);
+            if (s0 < s1) {
+                if (!started) {
+#pragma unroll
+                    for (int u = 0; u < X; ++u) win[u] = ring[((rbase + s0 + u) & RM) * 32 + lane];
+                    started = true;
+                }
+                for (int jb = s0; jb < s1; jb += X) {
+                    const int nb = (rbase + jb + X) & RM;
+#pragma unroll
+                    for (int u = 0; u < X; u += 2) {
+                        // taps of steps jb+u and jb+u+1 as two (k, k) pairs
+                        const ulonglong2 k2 = *reinterpret_cast<const ulonglong2*>(tb + (jb - jc + u));
+#pragma unroll
+                        for (int i = 0; i < X; ++i) {
+                            acc[i].x = ffma2(k2.x, win[(u + i) % X].x, acc[i].x);
+                            acc[i].y = ffma2(k2.x, win[(u + i) % X].y, acc[i].y);
+                        }
+                        win[u] = ring[(nb + u) * 32 + lane];
+#pragma unroll
+                        for (int i = 0; i < X; ++i) {
+                            acc[i].x = ffma2(k2.y, win[(u + 1 + i) % X].x, acc[i].x);
+                            acc[i].y = ffma2(k2.y, win[(u + 1 + i) % X].y, acc[i].y);
+                        }
+                        win[u + 1] = ring[(nb + u + 1) * 32 + lane];
+                    }
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+
+    if (wact) {
+        float* out;
+        long long out_row, out_cell;
+        const float* norm;
+        if (pass == 0) {
+            out = gr.H1; out_row = D; out_cell = (long long)gr.H * D;
+            norm = gr.table + lv.off_ny;
+        } else {
+            out = gr.T; out_row = ts; out_cell = (long long)gr.W * ts;
+            norm = gr.table + lv.off_nx;
+        }
+        long long ooff[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + 32 * k + lane;
+            ooff[k] = ok[k] ? (long long)(c / D) * out_cell + c % D : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < X; ++i) {
+            const int y = ylo + i;
+            if (y < R) {
+                const float nrm = norm[y];
+                float* orow = out + (long long)y * out_row;
+                const unsigned long long v[2] = {acc[i].x, acc[i].y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (ok[k])
+                        orow[ooff[k]] = __fdiv_rn(
+                            __uint_as_float((unsigned)(v[k >> 1] >> (32 * (k & 1)))), nrm);
+            }
+        }
+    }
+}
+
+int fir_ctas(int rows, int cols, int variant) {
+    const int ty = variant == kFirSmallRadius ? FirSmall::TY : FirLarge::TY;
+    return ((cols + kFirCols - 1) / kFirCols) * ((rows + ty - 1) / ty);
+}
+
+template <class TL>
+static size_t fir_smem() { return sizeof(ulonglong2) * TL::RING * 32; }
+
+static void fir_opt_in() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(fir_kernel<FirLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fir_smem<FirLarge>());
+    cudaFuncSetAttribute(fir_kernel<FirSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fir_smem<FirSmall>());
+    done[dev] = true;
+}
+
+void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
+                cudaStream_t s) {
+    if (ctas <= 0) return;
+    fir_opt_in();
+    if (variant == kFirSmallRadius)
+        fir_kernel<FirSmall><<<ctas, FirSmall::THREADS, fir_smem<FirSmall>(), s>>>(
+            pass, grids, map, D, grid_stride(D), target_stride(D));
+    else
+        fir_kernel<FirLarge><<<ctas, FirLarge::THREADS, fir_smem<FirLarge>(), s>>>(
+            pass, grids, map, D, grid_stride(D), target_stride(D));
+}
+
+}  // namespace plas

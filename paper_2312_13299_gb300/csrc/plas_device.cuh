@@ -13,6 +13,7 @@
 //     walking keeps the result inside [0, n).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -111,14 +112,31 @@ struct DevState {
     unsigned int arrivals;    // CTAs of the running assignment launch that finished
     int nonfinite;            // input held NaN / Inf
     int bad_index;            // a caller-supplied permutation entry was out of range
+    int pad_;
     long long grouped;        // cells that took part in a group, summed
     long long max_iters;      // 0 = none
+    // work of the iterations run (for the algorithmic roofline counts)
+    double fmas_y;            // in-range tap FMAs of the passes along y
+    double fmas_x;            // in-range tap FMAs of the passes along x
+    double beta2_sum;         // grouping-table entries generated
     unsigned int lo_bits[64]; // per-channel minimum, order-preserving encoding
     unsigned int hi_bits[64]; // per-channel maximum, order-preserving encoding
 };
 
-__device__ __forceinline__ bool state_idle(const DevState* st, int level) {
-    return st->done || st->level != level || (st->max_iters > 0 && st->it >= st->max_iters);
+// Bytes of the state the host reads back when it polls (everything before
+// the min/max encodings).
+constexpr size_t kStateHeaderBytes = offsetof(DevState, lo_bits);
+
+// In-range taps summed over every position of a pass of length len with
+// half-width r <= len - 1: sum_p (min(r, p) + min(r, len-1-p) + 1).
+__host__ __device__ inline double pass_taps(long long len, long long r) {
+    return (double)(len * (2 * r + 1) - r * (r + 1));
+}
+
+// A grid takes no further iteration once its schedule is done or its
+// iteration cap is reached.
+__device__ __forceinline__ bool sweep_idle(const DevState* st) {
+    return st->done || (st->max_iters > 0 && st->it >= st->max_iters);
 }
 
 // Order-preserving float <-> uint32 map (for exact atomic min / max).

@@ -1,0 +1,67 @@
+// plas_host.h -- host-side helpers shared by the C ABI translation units
+// (internal to the CUDA library).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/plas.h"
+#include "plas_kernels.h"
+
+namespace plas {
+
+// ---- errors -------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+int check_launch(const char* what);
+int num_sms();
+
+#define PLAS_CUDA(call)                                                                    \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::plas::fail(PLAS_ERR_CUDA, "%s failed: %s (%s:%d)", #call,             \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);               \
+    } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline bool channels_supported(int D) {
+    return (D >= 1 && D <= 16) || D == 20 || D == 24 || D == 32 || D == 48 || D == 64;
+}
+int validate_schedule(const plas_schedule& s);
+
+// ---- schedule geometry (Sec. 3.1) -----------------------------------------------
+// phi_L = phi0 * shrink^L while >= phi_min; r = floor(phi); beta = min(max(r +
+// 1, min_block), H, W); sigma = sigma_ratio * phi; taps k_j = (float) exp(-j^2 /
+// (2 sigma^2)) in FP64, stored twice each (pairs for the packed FMA).
+struct Geometry {
+    std::vector<LevelDesc> lv;
+    std::vector<float> table;  // padded tap pairs per level (norms filled on the device)
+    size_t table_floats = 0;
+};
+double start_radius(const plas_schedule& s, int H, int W);
+int count_levels(const plas_schedule& s, int H, int W);
+Geometry build_geometry(const plas_schedule& s, int H, int W);
+
+// ---- per-grid device workspace ----------------------------------------------------
+struct Workspace {
+    DevState* st;
+    GridRef* ref;  // the grid's own descriptor (one-grid sweeps)
+    float* G;
+    float* T;
+    float* H1;
+    uint32_t* pi;
+    LevelDesc* lv;
+    float* table;
+    double* macc;
+};
+size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Workspace* ws,
+                        char* base);
+size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
+
+// ---- pinned host staging for state polls (per host thread) ----------------------------
+int poll_buffers(size_t bytes, void** host, cudaEvent_t* ev2);
+
+}  // namespace plas

@@ -1,5 +1,11 @@
-// plas_kernels.h -- launch wrappers of the sort kernels (internal to the
-// CUDA library; the C ABI in plas_api.cu calls these).
+// plas_kernels.h -- kernels and launch wrappers of the PLAS sort (internal to
+// the CUDA library; the C ABI in plas_api.cu / batch.cu calls these).
+//
+// Every per-iteration kernel works on a list of grids (GridRef) and reads each
+// grid's current radius level from that grid's device state, so one launch
+// per kernel class advances every active grid by one iteration (a "sweep").
+// A CTA finds its grid through a per-launch map {grid, local CTA, CTAs of that
+// grid}; a single sort is the one-grid case with no map.
 #pragma once
 
 #include <cstddef>
@@ -11,80 +17,98 @@
 namespace plas {
 
 constexpr int kMaxD = 64;
-constexpr int kFirX = 8;  // outputs per thread of the FIR passes (register window)
+constexpr int kFirX = 8;       // outputs per lane and column of the FIR passes
+constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
+// FIR tilings (identical results): the small-radius one below this radius
+constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1;
+constexpr int kFirSmallRadiusLimit = 24;
+constexpr int kGroupThreads = 256;
+constexpr int kAssignThreads = 256;
 
 struct Weights {
     float w[kMaxD];
 };
 
-// Per-level blur geometry.  Row pass: taps padded on the left to a multiple of
-// kFirX ('rp' zeros before tap -r) and on the right to 'ntp' entries.
+// Per-level blur geometry.  Taps are stored as duplicated pairs (k, k), padded
+// on the left to a multiple of kFirX ('rp' zero taps before tap -r) and on the
+// right to 'ntp' entries; the border norms follow.
 struct LevelDesc {
     double phi;
     int r;      // floor(phi): blur half-width
     int beta;   // block side
-    int rx, rpx, ntpx;  // row pass: radius capped at W-1, left pad, padded taps
-    int ry, rpy, ntpy;  // column pass
-    long long off_tx, off_ty, off_nx, off_ny;  // offsets into the float table
+    int rx, rpx, ntpx;  // pass along x: radius capped at W-1, left pad, padded taps
+    int ry, rpy, ntpy;  // pass along y
+    long long off_tx, off_ty, off_nx, off_ny;  // float offsets into the level table
 };
+
+// One grid of a sweep.
+struct GridRef {
+    float* G;             // N x GS working grid (features, index, pad)
+    float* T;             // N x TS target
+    float* H1;            // N x D first-pass output, [x][y][d]
+    uint32_t* pi;         // grouping table (>= max beta^2 entries)
+    DevState* st;
+    const LevelDesc* lv;  // nlev entries
+    const float* table;   // level table (taps, norms)
+    int H, W;
+    int nlev;
+    int pad_;
+    uint64_t seed;
+    long long* trace_S;   // optional per-iteration residual sums
+    int* trace_level;     // optional per-iteration level
+    long long trace_cap;
+};
+
+// CTA -> grid map entry of a batched launch.
+struct CtaMap {
+    int grid;   // index into the GridRef array
+    int local;  // CTA index within that grid
+    int count;  // CTAs of that grid in this launch
+    int pad_;
+};
+
+struct CtaRef {
+    int g, local, count;
+};
+
+// The grid, CTA index within the grid and the grid's CTA count of this CTA
+// (no map: one grid, the whole launch).
+__device__ __forceinline__ CtaRef resolve_cta(const CtaMap* __restrict__ map) {
+    if (map == nullptr) return CtaRef{0, (int)blockIdx.x, (int)gridDim.x};
+    const CtaMap m = map[blockIdx.x];
+    return CtaRef{m.grid, m.local, m.count};
+}
 
 // Cell strides of the working grid G (features + index, padded to float4) and
 // of the target T (features, padded to float4).
 inline int grid_stride(int D) { return (D + 1 + 3) & ~3; }
 inline int target_stride(int D) { return (D + 3) & ~3; }
 
-// ---- preparation -----------------------------------------------------------
+// ---- CTA counts per grid ------------------------------------------------------
+int fir_ctas(int rows, int cols, int variant);  // rows = blur axis length, cols = cells * D
+int group_ctas(int H, int W, int num_sms);     // sized for the largest beta^2
+int assign_ctas(int H, int W, int num_sms);
+
+// ---- preparation (per grid) ----------------------------------------------------
 void launch_state_reset(DevState* st, cudaStream_t s);
 void launch_minmax(const float* x, long long N, int D, DevState* st, int num_sms,
                    cudaStream_t s);
 void launch_finalize_prep(DevState* st, long long N, int D, const Weights& w, int normalize,
                           cudaStream_t s);
 // mode 0: identity placement, 1: keyed random placement, 2: perm_init
-void launch_pack(const float* x, int N, int D, const Weights& w, int normalize,
-                 DevState* st, int mode, const int32_t* perm_init, uint64_t seed,
-                 float* G, cudaStream_t s);
+void launch_pack(const float* x, int N, int D, const Weights& w, int normalize, DevState* st,
+                 int mode, const int32_t* perm_init, uint64_t seed, float* G, cudaStream_t s);
 void launch_norms(const LevelDesc* lv_dev, int nlev, int H, int W, float* table,
                   cudaStream_t s);
 
-// ---- one iteration -----------------------------------------------------------
-struct RowPlan {
-    int dc;       // channels per CTA
-    int threads;  // 32 * dc
-    size_t smem;  // dynamic shared memory bytes
-};
-RowPlan plan_rows(int W, int D, int ntpx);
-void launch_blur_rows(const float* G, int gs, int H, int W, int D, float* H1,
-                      const DevState* st, int level, const LevelDesc& lv, const float* table,
-                      const RowPlan& plan, cudaStream_t s);
-
-struct ColPlan {
-    int ty;       // output rows per CTA
-    int threads;  // 32 * ty / kFirX
-    size_t smem;
-};
-ColPlan plan_cols(int H);
-void launch_blur_cols(const float* H1, int H, int W, int D, int ts, float* T,
-                      const DevState* st, int level, const LevelDesc& lv, const float* table,
-                      const ColPlan& plan, cudaStream_t s);
-
-void launch_group_table(uint64_t seed, const DevState* st, int level, int beta, uint32_t* pi,
-                        int num_sms, cudaStream_t s);
-
-struct AssignArgs {
-    float* G;
-    const float* T;
-    const uint32_t* pi;
-    DevState* st;
-    int H, W, D;
-    int level, beta, ngroups, nlevels;
-    uint64_t seed;
-    double tol;
-    long long* trace_S;   // optional per-iteration residual sums
-    int* trace_level;     // optional per-iteration level
-    long long trace_cap;
-};
-int assign_grid_size(int H, int W, int beta, int num_sms);
-void launch_assign(const AssignArgs& a, int grid, cudaStream_t s);
+// ---- one sweep (every grid in 'grids' advances by one iteration) --------------
+// map == nullptr: one grid (grids[0]), CTA index = blockIdx.x.
+void launch_group_table(const GridRef* grids, const CtaMap* map, int ctas, cudaStream_t s);
+// pass 0: along y (G -> H1), pass 1: along x (H1 -> T)
+void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
+                cudaStream_t s);
+void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
+                   cudaStream_t s);
 
 // ---- outputs -----------------------------------------------------------------
 void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream_t s);

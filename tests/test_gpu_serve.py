@@ -1,0 +1,102 @@
+"""Batched and served sorts (continuous batching) on the GPU.
+
+Each request's result -- permutation, carried attributes and final schedule
+state -- must equal the same request sorted alone with plas_sort, bit for bit,
+whether it ran in a static batch, arrived while others were running, or was
+admitted later because of the memory budget (every grid keeps its own
+counters and random streams)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_13299_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(48, 48), (17, 64), (64, 17), (33, 33), (96, 80), (128, 128), (20, 200)]
+
+
+def _requests(D=14, seed0=0):
+    out = []
+    for i, (H, W) in enumerate(SIZES):
+        x, c = synth.gaussians_3dgs(H * W, seed=seed0 + i)
+        out.append({"x": torch.from_numpy(x[:, :D].copy()).cuda(), "H": H, "W": W,
+                    "carried": torch.from_numpy(c).cuda(), "seed": 100 + i})
+    return out
+
+
+def _alone(plas, r):
+    return plas.sort(r["x"], r["H"], r["W"], carried=r["carried"], seed=r["seed"])
+
+
+def _same(a, b):
+    assert torch.equal(a.perm, b.perm)
+    assert torch.equal(a.carried, b.carried)
+    for k in ["it", "epoch", "redraws", "level", "done", "d_last", "d_prev"]:
+        assert a.state[k] == b.state[k], k
+
+
+def test_batch_sort_equals_alone(plas):
+    reqs = _requests()
+    res = plas.batch_sort(reqs)
+    for r, got in zip(reqs, res):
+        _same(got, _alone(plas, r))
+
+
+def test_batch_sort_d3(plas):
+    reqs = []
+    for i, (H, W) in enumerate([(64, 64), (40, 72), (16, 16), (5, 9)]):
+        reqs.append({"x": torch.from_numpy(synth.rgb_uniform(H, W, seed=i)).cuda(), "H": H,
+                     "W": W, "seed": i})
+    for r, got in zip(reqs, plas.batch_sort(reqs)):
+        one = plas.sort(r["x"], r["H"], r["W"], seed=r["seed"])
+        assert torch.equal(got.perm, one.perm) and got.state["it"] == one.state["it"]
+
+
+def test_server_arrivals_while_running(plas):
+    reqs = _requests(seed0=10)
+    srv = plas.Server(14)
+    tickets = {}
+    for r in reqs[:3]:
+        tickets[srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"])] = r
+    results = {}
+    steps = 0
+    late = list(reqs[3:])
+    while len(results) < len(reqs):
+        for t, res in srv.step(sweeps=4):
+            results[t] = res
+        steps += 1
+        if late and steps % 3 == 0:  # a request arrives while others are on the GPU
+            r = late.pop(0)
+            tickets[srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"])] = r
+        assert steps < 100000
+    srv.close()
+    for t, r in tickets.items():
+        _same(results[t], _alone(plas, r))
+
+
+def test_server_budget_admission(plas):
+    reqs = _requests(seed0=20)[:4]
+    need = max(plas.sort_workspace_bytes(r["H"], r["W"], 14) for r in reqs)
+    srv = plas.Server(14, mem_budget=need + 4096)
+    tickets = {srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"]): r for r in reqs}
+    results, max_active = {}, 0
+    while len(results) < len(reqs):
+        for t, res in srv.step(sweeps=16):
+            results[t] = res
+        q, a, mem = srv.status()
+        max_active = max(max_active, a)
+        assert mem <= need + 4096
+    srv.close()
+    assert max_active >= 1
+    for t, r in tickets.items():
+        _same(results[t], _alone(plas, r))
+
+
+def test_server_rejects_request_over_budget(plas):
+    srv = plas.Server(3, mem_budget=1024)
+    x = torch.rand(64 * 64, 3, device="cuda")
+    with pytest.raises(RuntimeError) as e:
+        srv.submit(x, 64, 64)
+    assert "budget" in str(e.value)
+    srv.close()
