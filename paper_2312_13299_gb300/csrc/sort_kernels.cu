@@ -172,7 +172,7 @@ __device__ void schedule_step(DevState* st, long long N, int nby, int nbx, int n
 }
 
 template <int D>
-__global__ void __launch_bounds__(kAssignThreads) assign_kernel(
+__global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, double tol) {
     constexpr int GS = (D + 1 + 3) & ~3, TS = (D + 3) & ~3;
     __shared__ unsigned long long s_part[kAssignThreads / 32];
@@ -201,15 +201,24 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(
     const long long nwarps = ((long long)cr.count * kAssignThreads) >> 5;
     constexpr Perm24 kPerm24 = make_perm24();
     // ---- groups: 8 per warp ----
+    // the grouping-table entries of the next iteration are read one iteration
+    // ahead, so each iteration waits for one memory round trip, not two
+    auto group_of = [&](long long b) -> int {
+        const long long t = b + (lane >> 2);
+        return t < ngt ? (int)(t % ngroups) : 0;
+    };
+    uint4 l4_next = make_uint4(0u, 0u, 0u, 0u);
+    if (gwarp * 8 < ngt) l4_next = __ldg(reinterpret_cast<const uint4*>(pi) + group_of(gwarp * 8));
     for (long long base = gwarp * 8; base < ngt; base += nwarps * 8) {
         const long long task0 = base + (lane >> 2);
         const bool active = task0 < ngt;
         const long long task = active ? task0 : 0;
         const long long blk = task / ngroups;
-        const int g = (int)(task - blk * ngroups);
         const int by = (int)(blk / nbx), bx = (int)(blk - (long long)by * nbx);
         const int oy = dy + by * beta, ox = dx + bx * beta;
-        const uint4 l4 = __ldg(reinterpret_cast<const uint4*>(pi) + g);
+        const uint4 l4 = l4_next;
+        if (base + nwarps * 8 < ngt)
+            l4_next = __ldg(reinterpret_cast<const uint4*>(pi) + group_of(base + nwarps * 8));
         const uint32_t ls[4] = {l4.x, l4.y, l4.z, l4.w};
         int pos[4];
 #pragma unroll
