@@ -70,7 +70,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha1()
-    with open(os.path.join(ROOT, "paper_2312_13299_gb300", "csrc", "sort_kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2312_13299_gb300", "csrc", "fir_kernels.cu"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:12]
 
@@ -290,24 +290,33 @@ def run_plas(args):
 
     for _ in range(args.warmup):
         step(False)
-    torch.cuda.synchronize()
-    _barrier(pg)
-    clocks = ClockSampler(local)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    _barrier(pg)
-    e0.record(stream)
-    stats = [step(True).stats for _ in range(args.steps)]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    _barrier(pg)
-    elapsed_ms = e0.elapsed_time(e1)
-    ck = clocks.stop()
-    max_ms = _max_over_ranks(elapsed_ms, pg, dev)
+
+    def timed(profile):
+        """K sorts bracketed by barrier + synchronize; CUDA events on the
+        launching stream; clocks sampled meanwhile."""
+        torch.cuda.synchronize()
+        _barrier(pg)
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        _barrier(pg)
+        e0.record(stream)
+        sts = [step(profile).stats for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(pg)
+        ck = clocks.stop()
+        return _max_over_ranks(e0.elapsed_time(e1), pg, dev), sts, ck
+
+    # the measured value: plain sorts, no per-kernel events
+    max_ms, stats_plain, ck = timed(False)
     ms_per_sort = max_ms / (args.steps * world)
-    launches = int(sum(st["launches"] for st in stats))
+    launches = int(sum(st["launches"] for st in stats_plain))
+    # per-kernel durations for the roofline: the same K sorts again with a
+    # CUDA event pair around every launch (their own timed region)
+    prof_ms, stats, ck_prof = timed(True)
 
     # end to end: pinned host inputs in, permutation + carried out, per step
     xh = torch.from_numpy(x_np).pin_memory()
@@ -340,8 +349,10 @@ def run_plas(args):
             pg.destroy_process_group()
         return
     peaks, psrc = _peaks()
-    rl, per_kernel = roofline(stats, peaks, psrc, ck, args.workload)
-    st0 = stats[-1]
+    rl, per_kernel = roofline(stats, peaks, psrc, ck_prof or ck, args.workload)
+    rl["timing"] = (f"CUDA events around every launch over {args.steps} further sorts "
+                    f"({prof_ms / args.steps:.1f} ms per sort with the events)")
+    st0 = stats_plain[-1]
     line = {
         "metric": METRIC, "value": round(ms_per_sort, 3), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
@@ -417,10 +428,14 @@ def run_reference(args):
 
 
 def run_serve(args):
-    """Served stream: n requests with Poisson arrivals (sides U{128..1024}, 14
-    sort + 45 carried channels), continuous batching under a 40 GB admission
-    budget vs the plain path (one plas_sort per request, first come first
-    served).  Latency = completion time - arrival time (host clock)."""
+    """Served stream: n requests (sides U{128..1024}, 14 sort + 45 carried
+    channels) under a 40 GB admission budget, through the server (continuous
+    batching, one run per scheduling policy) and through the plain path (one
+    plas_sort per request, first come first served).  Two arrival patterns:
+    Poisson arrivals at 0.8 x the plain path's capacity (mean service time of
+    the side distribution, from a power-law fit of measured plain sorts), and a
+    burst (every request at t = 0) for throughput.  Latency = completion time -
+    arrival time (host clock)."""
     import numpy as np
     import torch
     import paper_2312_13299_gb300 as plas
@@ -428,27 +443,31 @@ def run_serve(args):
     plas.load()
     dev = torch.device("cuda", 0)
     n = args.requests
-    # offered load: arrivals at 0.8 x the plain path's service rate (measured
-    # on a 576x576 request, the mean cell count of U{128..1024} sides)
-    xm, cm = synth.gaussians_3dgs(576 * 576, seed=999)
-    xm_t, cm_t = torch.from_numpy(xm).to(dev), torch.from_numpy(cm).to(dev)
-    plas.sort(xm_t, 576, 576, carried=cm_t)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    plas.sort(xm_t, 576, 576, carried=cm_t)
-    torch.cuda.synchronize()
-    mean_service = time.perf_counter() - t
+    # plain service time vs side: t = a * side^b
+    fit_sides = [128, 384, 768]
+    ts = []
+    for side in fit_sides:
+        xm, cm = synth.gaussians_3dgs(side * side, seed=999)
+        xm_t, cm_t = torch.from_numpy(xm).to(dev), torch.from_numpy(cm).to(dev)
+        plas.sort(xm_t, side, side, carried=cm_t)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        plas.sort(xm_t, side, side, carried=cm_t)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t)
+    b, loga = np.polyfit(np.log(fit_sides), np.log(ts), 1)
+    mean_service = float(np.mean([math.exp(loga) * sd ** b for sd in range(128, 1025)]))
     rate = 0.8 / mean_service
-    stream = synth.request_stream(n, seed=0, rate_per_s=rate)
-    reqs = []
-    for i, (arr, side) in enumerate(stream):
+    base = synth.request_stream(n, seed=0, rate_per_s=rate)
+    inputs = []
+    for i, (_, side) in enumerate(base):
         x, c = synth.gaussians_3dgs(side * side, seed=1000 + i)
-        reqs.append((arr, side, torch.from_numpy(x).to(dev), torch.from_numpy(c).to(dev), i))
+        inputs.append((side, torch.from_numpy(x).to(dev), torch.from_numpy(c).to(dev), i))
     torch.cuda.synchronize()
 
-    def plain():
+    def plain(arrivals):
         lat, t0, cells_iters = [], time.perf_counter(), 0
-        for arr, side, x, c, i in reqs:
+        for arr, (side, x, c, i) in zip(arrivals, inputs):
             while time.perf_counter() - t0 < arr:
                 time.sleep(0.0005)
             r = plas.sort(x, side, side, carried=c, seed=i)
@@ -457,14 +476,14 @@ def run_serve(args):
             cells_iters += side * side * r.state["it"]
         return lat, time.perf_counter() - t0, cells_iters
 
-    def served():
-        srv = plas.Server(14, mem_budget=40 * 10 ** 9)
+    def served(arrivals, policy):
+        srv = plas.Server(14, mem_budget=40 * 10 ** 9, policy=policy)
         lat, t0, nxt, pending, cells_iters = {}, time.perf_counter(), 0, {}, 0
         while len(lat) < n:
             now = time.perf_counter() - t0
-            while nxt < n and reqs[nxt][0] <= now:
-                arr, side, x, c, i = reqs[nxt]
-                pending[srv.submit(x, side, side, c, seed=i)] = (arr, side)
+            while nxt < n and arrivals[nxt] <= now:
+                side, x, c, i = inputs[nxt]
+                pending[srv.submit(x, side, side, c, seed=i)] = (arrivals[nxt], side)
                 nxt += 1
             if not pending:
                 time.sleep(0.0005)
@@ -476,22 +495,34 @@ def run_serve(args):
         srv.close()
         return list(lat.values()), time.perf_counter() - t0, cells_iters
 
-    out = {}
-    for name, fn in [("plain", plain), ("served", served)]:
-        lat, wall, ci = fn()
+    def summary(lat, wall, ci):
         lat = np.array(lat) * 1e3
-        out[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 1),
-                     "p99_ms": round(float(np.percentile(lat, 99)), 1),
-                     "mean_ms": round(float(lat.mean()), 1), "wall_s": round(wall, 2),
-                     "requests_per_s": round(n / wall, 3),
-                     "melem_iter_per_s": round(ci / wall / 1e6, 1)}
-    line = {"metric": "served p50/p99 latency of PLAS sort requests", "value": out["served"]["p99_ms"],
-            "unit": "ms (p99, served)", "higher_is_better": False, "n_gpus": 1,
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 1),
+                "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                "mean_ms": round(float(lat.mean()), 1), "wall_s": round(wall, 2),
+                "requests_per_s": round(n / wall, 3), "melem_iter_per_s": round(ci / wall / 1e6, 1)}
+
+    patterns = {"poisson": [a for a, _ in base], "burst": [0.0] * n}
+    policies = [p for p in args.policies.split(",") if p]
+    out = {}
+    for pat in [p for p in args.patterns.split(",") if p]:
+        arr = patterns[pat]
+        out[pat] = {"plain": summary(*plain(arr))}
+        for pol in policies:
+            out[pat]["served_" + pol] = summary(*served(arr, pol))
+    first = policies[0] if policies else None
+    head = out.get("poisson", out.get("burst", {}))
+    line = {"metric": "served p50/p99 latency of PLAS sort requests",
+            "value": head.get("served_" + first, {}).get("p99_ms") if first else None,
+            "unit": f"ms (p99, served, {first})", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic (seeded numpy; 3DGS-shaped attributes)",
-            "config": {"workload": f"{n} requests, Poisson arrivals at 0.8 x plain service rate "
-                                   f"({rate:.2f}/s), sides U{{128..1024}}, 14 sort + 45 carried fp32, "
-                                   "40 GB admission budget", "sweeps_per_step": args.sweeps},
-            "served": out["served"], "plain": out["plain"]}
+            "config": {"workload": f"{n} requests, sides U{{128..1024}}, 14 sort + 45 carried fp32, "
+                                   "40 GB admission budget",
+                       "poisson_rate_per_s": round(rate, 3),
+                       "plain_service_fit": f"t = {math.exp(loga):.3g} * side^{b:.2f} s "
+                                            f"(mean {mean_service * 1e3:.0f} ms over the side distribution)",
+                       "sweeps_per_step": args.sweeps},
+            "results": out}
     print(json.dumps(line), flush=True)
 
 
@@ -534,6 +565,9 @@ def main():
                     help="served-stream benchmark (continuous batching vs plain), own JSON line")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
+    ap.add_argument("--policies", default="fifo_fill,shortest_first,all",
+                    help="with --serve: server policies to run")
+    ap.add_argument("--patterns", default="poisson,burst", help="with --serve: arrival patterns")
     args = ap.parse_args()
     if args.ncu_case > 0:
         run_ncu_case(args)

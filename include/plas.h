@@ -63,12 +63,17 @@ typedef struct plas_schedule {
     int normalize;      /* 1: per-channel [0,1] normalisation before the     */
                         /* weights (Sec. 3.1); 0: weights only               */
     int iters_per_poll; /* iterations enqueued between two host reads of the */
-                        /* 64-byte device state; <= 0 selects 8              */
+                        /* 128-byte device state header; <= 0 selects 8      */
     long long max_iters;/* stop once the iteration counter reaches this;     */
                         /* 0 = run the full schedule                         */
     int profile;        /* 1: time every kernel class with CUDA events and   */
-                        /* report it in plas_stats (adds event records)      */
-    int reserved;
+                        /* report it in plas_stats (adds event records;      */
+                        /* implies direct launches)                          */
+    int graphs;         /* 1: each batch of iters_per_poll iterations is     */
+                        /* captured once as a CUDA graph and replayed (the   */
+                        /* kernels read the level from device state, so one  */
+                        /* graph serves every level); 0: direct launches.    */
+                        /* Identical results either way.                     */
     long long* trace_S; /* device or NULL: trace_S[it] = fixed-point residual */
                         /* sum of iteration it (mean L2 distance * N * 2^k)  */
     int* trace_level;   /* device or NULL: level of iteration it             */
@@ -94,8 +99,10 @@ typedef struct plas_state {
 /* kernel classes reported by plas_stats.kernel[] */
 #define PLAS_K_PREP 0     /* min/max, normalise, initial placement           */
 #define PLAS_K_BLUR_ROWS 1/* target, pass along x                            */
-#define PLAS_K_BLUR_COLS 2/* target, pass along y                            */
-#define PLAS_K_GROUPS 3   /* grouping permutation of the block cells         */
+#define PLAS_K_BLUR_COLS 2/* target, pass along y (its launches also write    */
+                          /* the iteration's grouping permutation)           */
+#define PLAS_K_GROUPS 3   /* grouping permutation of the block cells: no     */
+                          /* launches of its own (part of BLUR_COLS)         */
 #define PLAS_K_ASSIGN 4   /* 24-permutation scoring, swap, residual, schedule */
 #define PLAS_K_GATHER 5   /* permutation + carried-attribute gather          */
 #define PLAS_K_COUNT 6
@@ -119,6 +126,8 @@ typedef struct plas_stats {
     long long launches;     /* kernel launches made by the call (idle ones    */
                             /* after a level change included)                 */
     plas_kernel_stat kernel[PLAS_K_COUNT]; /* filled when schedule.profile=1  */
+    long long graph_launches; /* CUDA graph replays (batches of sweeps)       */
+    long long graph_captures; /* graphs captured (0 with direct launches)     */
 } plas_stats;
 
 /* Fill *out with the defaults above.  Returns PLAS_OK, or
@@ -336,18 +345,32 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   stay valid until the request completes) and returns its ticket (0, 1,
  *   ...).  PLAS_ERR_BUDGET if the request alone exceeds mem_budget,
  *   PLAS_ERR_INVALID_ARG for a bad descriptor.
- * plas_server_step: admits queued requests that fit, runs up to 'sweeps'
- *   sweeps over the admitted grids, and reports in done[0..*n_done) (at most
- *   'cap') the tickets whose outputs are complete on return (the call waits
- *   for the stream).  A finished request's workspace is released before the
- *   next admission.  job->state_out, if given, is filled on completion.
+ * plas_server_step: admits queued requests that fit, enqueues 'sweeps'
+ *   sweeps over the grids the policy chooses, and reports in
+ *   done[0..*n_done) (at most 'cap') the tickets whose outputs are complete
+ *   on return.  The call does not wait for the sweeps it enqueues: it reads
+ *   the grids' state one step behind, so a request is reported a step or two
+ *   after its last iteration, and the GPU stays busy while the host runs.
+ *   It waits for the stream only when no grid is left to sweep.  A finished
+ *   request's workspace is released (stream-ordered) before the next
+ *   admission.  job->state_out, if given, is filled on completion.
+ * plas_server_set_policy: which admitted grids each step's sweeps advance
+ *   (results are the same under every policy; only the timing differs):
+ *   PLAS_SERVE_FIFO_FILL (default): in admission order until the estimated
+ *     time of one sweep over the chosen grids reaches 0.6 ms (one grid at a
+ *     large radius fills a sweep; grids at small radii share one);
+ *   PLAS_SERVE_SHORTEST_FIRST: least estimated work left first, same fill;
+ *   PLAS_SERVE_ALL: every admitted grid in every sweep.
+ *   PLAS_ERR_INVALID_ARG for an unknown policy.
  * plas_server_status: queued and admitted requests, device bytes in use.
  * plas_server_destroy: waits for the stream and frees everything; requests
  *   still queued or running are abandoned (their outputs are undefined).
  */
 typedef struct plas_server plas_server;
+enum { PLAS_SERVE_FIFO_FILL = 0, PLAS_SERVE_SHORTEST_FIRST = 1, PLAS_SERVE_ALL = 2 };
 int plas_server_create(int D, const float* weights, const plas_schedule* sched,
                        size_t mem_budget, void* stream, plas_server** out);
+int plas_server_set_policy(plas_server* srv, int policy);
 int plas_server_submit(plas_server* srv, const plas_job* job, long long* ticket);
 int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap, int* n_done);
 int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use);

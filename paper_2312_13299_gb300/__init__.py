@@ -43,6 +43,7 @@ class Schedule:
     iters_per_poll: int = 8
     max_iters: int = 0
     profile: bool = False
+    graphs: bool = True
 
     def to_c(self, trace_S: Optional[torch.Tensor] = None,
              trace_level: Optional[torch.Tensor] = None) -> _lib.plas_schedule:
@@ -51,6 +52,7 @@ class Schedule:
         s.sigma_ratio, s.min_block = self.sigma_ratio, self.min_block
         s.shuffle_init, s.normalize = int(self.shuffle_init), int(self.normalize)
         s.iters_per_poll, s.max_iters, s.profile = self.iters_per_poll, self.max_iters, int(self.profile)
+        s.graphs = int(self.graphs)
         s.trace_S = trace_S.data_ptr() if trace_S is not None else None
         s.trace_level = trace_level.data_ptr() if trace_level is not None else None
         cap = 0
@@ -236,11 +238,15 @@ def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] 
 class Server:
     """Continuous batching of sort requests (plas_server_*): requests queue up,
     are admitted while their workspaces fit the device-memory budget, and
-    advance together one iteration per sweep.  Results equal sort() of each
-    request alone.  All work runs on the stream current at construction."""
+    advance together one iteration per sweep; 'policy' picks which admitted
+    grids each step advances (fifo_fill, shortest_first, all).  Results equal
+    sort() of each request alone under every policy.  All work runs on the
+    stream current at construction."""
+
+    POLICIES = {"fifo_fill": 0, "shortest_first": 1, "all": 2}
 
     def __init__(self, D: int, weights=None, schedule: Optional[Schedule] = None,
-                 mem_budget: int = 0, device=None):
+                 mem_budget: int = 0, device=None, policy: str = "fifo_fill"):
         self._lib = load()
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
@@ -255,6 +261,11 @@ class Server:
         check(rc, "plas_server_create")
         self._h = h
         self._live = {}
+        if policy not in self.POLICIES:
+            self.close()
+            raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
+        check(self._lib.plas_server_set_policy(self._h, self.POLICIES[policy]),
+              "plas_server_set_policy")
 
     def submit(self, x: torch.Tensor, H: int, W: int, carried: Optional[torch.Tensor] = None,
                seed: int = 0) -> int:

@@ -32,7 +32,7 @@ class plas_schedule(ctypes.Structure):
     _fields_ = [("phi0", c_double), ("shrink", c_double), ("phi_min", c_double),
                 ("tol", c_double), ("sigma_ratio", c_double), ("min_block", c_int),
                 ("shuffle_init", c_int), ("normalize", c_int), ("iters_per_poll", c_int),
-                ("max_iters", c_ll), ("profile", c_int), ("reserved", c_int),
+                ("max_iters", c_ll), ("profile", c_int), ("graphs", c_int),
                 ("trace_S", c_void_p), ("trace_level", c_void_p), ("trace_cap", c_ll)]
 
 
@@ -53,7 +53,8 @@ class plas_stats(ctypes.Structure):
     _fields_ = [("iterations", c_ll), ("redraws", c_ll), ("grouped_cells", c_ll),
                 ("levels", c_int), ("status", c_int), ("final_l2_to_target", c_double),
                 ("neighbour_l2", c_double), ("ms_total", c_double), ("launches", c_ll),
-                ("kernel", plas_kernel_stat * K_COUNT)]
+                ("kernel", plas_kernel_stat * K_COUNT), ("graph_launches", c_ll),
+                ("graph_captures", c_ll)]
 
 
 class plas_job(ctypes.Structure):
@@ -92,6 +93,7 @@ SIGNATURES = {
                                 c_void_p, c_size_t, c_void_p]),
     "plas_server_create": (c_int, [c_int, P(c_float), P(plas_schedule), c_size_t, c_void_p,
                                    P(c_void_p)]),
+    "plas_server_set_policy": (c_int, [c_void_p, c_int]),
     "plas_server_submit": (c_int, [c_void_p, P(plas_job), P(c_ll)]),
     "plas_server_step": (c_int, [c_void_p, c_int, P(c_ll), c_int, P(c_int)]),
     "plas_server_status": (c_int, [c_void_p, P(c_int), P(c_int), P(c_size_t)]),

@@ -5,7 +5,7 @@
 // Morgenstern et al., arXiv 2312.13299): grouping table, target pass along y,
 // target pass along x, assignment + schedule step -- one launch per kernel
 // class for all grids.  The schedule runs on the device, so the host only
-// enqueues batches of sweeps and reads each grid's 150-byte state header back
+// enqueues batches of sweeps and reads each grid's 128-byte state header back
 // once per batch, one batch behind (the GPU never waits for the host inside a
 // level).  A grid whose schedule has ended takes no work in later sweeps; its
 // outputs (permutation, carried attributes) are gathered when the host sees
@@ -23,7 +23,8 @@ namespace plas {
 
 namespace {
 
-enum { kClsGroups = 0, kClsFirY = 1, kClsFirX = 2, kClsAssign = 3, kClsCount = 4 };
+// kernel classes of a sweep (the grouping table is written by the FIR pass-0 launch)
+enum { kClsFirY = 0, kClsFirX = 1, kClsAssign = 2, kClsCount = 3 };
 
 struct Job {
     const float* x = nullptr;
@@ -53,11 +54,15 @@ struct Slot {
     bool owns = false;
     long long N = 0;
     int nlev = 0;
-    int ctas[kClsCount] = {0, 0, 0, 0};
+    int ctas[kClsCount] = {0, 0, 0};
     bool active = false;
     DevState last{};
     long long last_it = -1;
     int stuck = 0;
+    // served scheduling: estimated device time of one iteration at each level
+    // and of the rest of the sort from each level on (ns)
+    std::vector<double> it_ns;
+    std::vector<double> rem_ns;
 };
 
 bool finished(const Slot& s, const plas_schedule& sch) {
@@ -67,6 +72,26 @@ bool finished(const Slot& s, const plas_schedule& sch) {
 struct EventPair {
     cudaEvent_t a, b;
     int cls;
+};
+
+// Launch parameters of one batch of sweeps.
+struct SweepPlan {
+    int k;
+    int var;
+    const GridRef* grids;
+    const CtaMap* map[kClsCount];
+    int ctas[kClsCount];
+    bool operator==(const SweepPlan& o) const {
+        if (k != o.k || var != o.var || grids != o.grids) return false;
+        for (int c = 0; c < kClsCount; ++c)
+            if (map[c] != o.map[c] || ctas[c] != o.ctas[c]) return false;
+        return true;
+    }
+};
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    SweepPlan plan{};
 };
 
 class Engine {
@@ -82,6 +107,9 @@ class Engine {
         for (auto e : ev_)
             if (e) cudaEventDestroy(e);
         if (dmaps_ && dmaps_owned_) cudaFreeAsync(dmaps_, st_);
+        for (auto& g : graph_)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (cap_) cudaStreamDestroy(cap_);
     }
 
     // Multi-grid descriptor arrays come from this arena when given (no
@@ -138,7 +166,6 @@ class Engine {
         end(e0, -1);
         launches_ += 5;
         if (int e = check_launch("preparation")) return e;
-        sl->ctas[kClsGroups] = group_ctas(H, W, nsm_);
         sl->ctas[kClsFirY] = fir_ctas(H, W * D_, kFirLargeRadius);
         sl->ctas[kClsFirX] = fir_ctas(W, H * D_, kFirLargeRadius);
         sl->ctas[kClsAssign] = assign_ctas(H, W, nsm_);
@@ -154,37 +181,41 @@ class Engine {
         if (active_.empty()) return PLAS_OK;
         if (dirty_)
             if (int e = rebuild()) return e;
+        SweepPlan p{};
+        p.k = k;
         const bool one = active_.size() == 1;
-        const GridRef* grids = one ? active_[0]->ws.ref : dgrids_;
+        p.grids = one ? active_[0]->ws.ref : dgrids_;
         // FIR tiling: one grid follows the radius it last reported (both tilings
         // give the same bits; a stale choice only costs time); many grids use
         // the large-radius tiling their CTA maps were built for
-        int var = kFirLargeRadius;
-        int fir_ctas_one[2] = {0, 0};
+        p.var = kFirLargeRadius;
+        for (int c = 0; c < kClsCount; ++c) {
+            p.map[c] = one ? nullptr : dmap_[c];
+            p.ctas[c] = one ? active_[0]->ctas[c] : total_[c];
+        }
         if (one) {
             const Slot* sl = active_[0];
             const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
-            var = sl->geo.lv[L].r < kFirSmallRadiusLimit ? kFirSmallRadius : kFirLargeRadius;
-            fir_ctas_one[0] = fir_ctas(sl->job.H, sl->job.W * D_, var);
-            fir_ctas_one[1] = fir_ctas(sl->job.W, sl->job.H * D_, var);
+            p.var = sl->geo.lv[L].r < kFirSmallRadiusLimit ? kFirSmallRadius : kFirLargeRadius;
+            p.ctas[kClsFirY] = fir_ctas(sl->job.H, sl->job.W * D_, p.var);
+            p.ctas[kClsFirX] = fir_ctas(sl->job.W, sl->job.H * D_, p.var);
         }
-        for (int i = 0; i < k; ++i) {
-            for (int c = 0; c < kClsCount; ++c) {
-                const CtaMap* map = one ? nullptr : dmap_[c];
-                int ctas = one ? active_[0]->ctas[c] : total_[c];
-                if (one && c == kClsFirY) ctas = fir_ctas_one[0];
-                if (one && c == kClsFirX) ctas = fir_ctas_one[1];
-                cudaEvent_t e0 = begin();
-                switch (c) {
-                    case kClsGroups: launch_group_table(grids, map, ctas, st_); break;
-                    case kClsFirY: launch_fir(0, grids, map, ctas, D_, var, st_); break;
-                    case kClsFirX: launch_fir(1, grids, map, ctas, D_, var, st_); break;
-                    default: launch_assign(grids, map, ctas, D_, s_.tol, st_); break;
-                }
-                end(e0, c);
+        launches_ += (long long)k * kClsCount;
+        if (s_.graphs && !s_.profile && !graphs_failed_) {
+            // every kernel reads its grid's level from device state, so a batch
+            // captured once replays unchanged until the grid set, the tiling or
+            // k changes
+            Graph& g = graph_[p.var];
+            if (!g.exec || !(g.plan == p)) {
+                if (int e = capture(p, &g)) return e;
             }
-            launches_ += kClsCount;
+            if (g.exec) {
+                PLAS_CUDA(cudaGraphLaunch(g.exec, st_));
+                graph_launches_ += 1;
+                return PLAS_OK;
+            }
         }
+        enqueue(p, st_, true);
         return check_launch("sweep");
     }
 
@@ -240,7 +271,7 @@ class Engine {
             }
         }
         sl->active = false;
-        active_.erase(std::find(active_.begin(), active_.end(), sl));
+        active_.erase(std::remove(active_.begin(), active_.end(), sl), active_.end());
         dirty_ = true;
         return check_launch("outputs");
     }
@@ -261,7 +292,6 @@ class Engine {
 
     static int class_to_stat(int c) {
         switch (c) {
-            case kClsGroups: return PLAS_K_GROUPS;
             case kClsFirY: return PLAS_K_BLUR_COLS;
             case kClsFirX: return PLAS_K_BLUR_ROWS;
             default: return PLAS_K_ASSIGN;
@@ -269,6 +299,14 @@ class Engine {
     }
 
     std::vector<Slot*>& active() { return active_; }
+    // Replace the set of grids the next sweeps advance (admitted slots only).
+    void select(const std::vector<Slot*>& run) {
+        if (run != active_) {
+            active_ = run;
+            dirty_ = true;
+        }
+    }
+    const std::vector<Slot*>& polled(int buf) const { return polled_[buf]; }
     plas_kernel_stat ks_[PLAS_K_COUNT] = {};
     long long launches_ = 0;
 
@@ -294,6 +332,62 @@ class Engine {
         cudaEvent_t e = nullptr;
         cudaEventCreate(&e);
         return e;
+    }
+
+    // The launches of k sweeps (events only when profiling directly).
+    void enqueue(const SweepPlan& p, cudaStream_t st, bool events) {
+        for (int i = 0; i < p.k; ++i) {
+            for (int c = 0; c < kClsCount; ++c) {
+                cudaEvent_t e0 = events ? begin() : nullptr;
+                switch (c) {
+                    case kClsFirY: launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st); break;
+                    case kClsFirX: launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st); break;
+                    default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st); break;
+                }
+                if (events) end(e0, c);
+            }
+        }
+    }
+
+    // Capture the launches of plan p on a private stream (nothing runs) and
+    // instantiate them.  A capture the runtime refuses leaves g empty and
+    // switches this engine to direct launches; a launch error fails.
+    int capture(const SweepPlan& p, Graph* g) {
+        if (g->exec) {
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+        if (!cap_) PLAS_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+        prepare_fir_launches();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            graphs_failed_ = true;
+            return PLAS_OK;
+        }
+        enqueue(p, cap_, false);
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ce = cudaStreamEndCapture(cap_, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(PLAS_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(le));
+        }
+        if (ce != cudaSuccess || !graph) {
+            cudaGetLastError();
+            graphs_failed_ = true;
+            return PLAS_OK;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            g->exec = nullptr;
+            graphs_failed_ = true;
+            return PLAS_OK;
+        }
+        g->plan = p;
+        captures_ += 1;
+        return PLAS_OK;
     }
 
     int host_buffers(size_t bytes) {
@@ -380,14 +474,21 @@ class Engine {
     size_t dmaps_cap_ = 0;
     bool dmaps_owned_ = false;
     GridRef* dgrids_ = nullptr;
-    CtaMap* dmap_[kClsCount] = {nullptr, nullptr, nullptr, nullptr};
-    int total_[kClsCount] = {0, 0, 0, 0};
+    CtaMap* dmap_[kClsCount] = {nullptr, nullptr, nullptr};
+    int total_[kClsCount] = {0, 0, 0};
     char* host_ = nullptr;
     size_t host_cap_ = 0;
     char* polled_base_[2] = {nullptr, nullptr};
     cudaEvent_t ev_[2] = {nullptr, nullptr};
     std::vector<EventPair> marks_;
     std::vector<cudaEvent_t> pool_;
+    cudaStream_t cap_ = nullptr;
+    Graph graph_[2];  // one per FIR tiling
+    bool graphs_failed_ = false;
+
+   public:
+    long long captures_ = 0;
+    long long graph_launches_ = 0;
 };
 
 int status_error(const DevState& st) {
@@ -570,12 +671,15 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
                 stats->kernel[PLAS_K_BLUR_COLS].flops = 2.0 * fin.fmas_y;
                 stats->kernel[PLAS_K_BLUR_ROWS].bytes = its * 8.0 * (double)N * D;
                 stats->kernel[PLAS_K_BLUR_ROWS].flops = 2.0 * fin.fmas_x;
-                stats->kernel[PLAS_K_GROUPS].bytes = 4.0 * fin.beta2_sum;
+                // the grouping table is written by the pass-0 launches
+                stats->kernel[PLAS_K_BLUR_COLS].bytes += 4.0 * fin.beta2_sum;
                 stats->kernel[PLAS_K_ASSIGN].bytes =
                     (double)fin.grouped * (12.0 * D + 8.0) + (its * N - (double)fin.grouped) * 8.0 * D;
                 stats->kernel[PLAS_K_GATHER].bytes = (double)N * 8 + (carried_out ? (double)N * C * 8 : 0.0) +
                                                      (sorted_out ? (double)N * D * 8 : 0.0);
                 stats->launches = eng.launches_;
+                stats->graph_launches = eng.graph_launches_;
+                stats->graph_captures = eng.captures_;
             }
         } else if (rc == PLAS_OK) {
             if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PLAS_ERR_CUDA, "stream sync failed");
@@ -604,7 +708,7 @@ static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedul
         if (per_job) (*per_job)[i] = b;
         total += b;
         grids += 1;
-        ctas += group_ctas(H, W, nsm) + fir_ctas(H, W * D, kFirLargeRadius) +
+        ctas += fir_ctas(H, W * D, kFirLargeRadius) +
                 fir_ctas(W, H * D, kFirLargeRadius) + assign_ctas(H, W, nsm);
     }
     if (maps_at) *maps_at = total;
@@ -694,12 +798,77 @@ struct plas_server {
     size_t budget = 0;
     size_t in_use = 0;
     cudaStream_t st = nullptr;
+    int policy = PLAS_SERVE_FIFO_FILL;
     std::unique_ptr<Engine> eng;
     std::deque<std::unique_ptr<Slot>> queue;
-    std::vector<std::unique_ptr<Slot>> running;
+    std::vector<std::unique_ptr<Slot>> running;  // admitted, in admission order
+    struct Retiring {
+        cudaEvent_t ev;
+        Slot* sl;
+    };
+    std::vector<Retiring> retiring;  // outputs enqueued, not yet known complete
+    // host records of finished requests, kept until no read-back in flight
+    // can name them
+    std::vector<std::pair<long long, std::unique_ptr<Slot>>> graveyard;
+    std::vector<cudaEvent_t> events;
     std::vector<long long> completed;  // finished, not yet reported
     long long next_ticket = 0;
+    long long step_no = 0;
+    int buf = 0;
+    bool pending = false;  // a state read-back is in flight
 };
+
+namespace {
+
+// Estimated device time of the rest of a sort from each level on: per level
+// about 53 iterations (the mean of measured full schedules), each costing the
+// two target passes (4 flops per in-range tap and channel, at the ~43 TFLOP/s
+// the FIR kernel sustains), the assignment (~0.06 ns per cell) and a launch
+// floor of 15 us.  Only the order of these numbers matters.
+void plan_slot(Slot* sl, int D) {
+    const double N = (double)sl->N;
+    const int H = sl->job.H, W = sl->job.W;
+    sl->it_ns.assign(sl->nlev, 0.0);
+    sl->rem_ns.assign(sl->nlev + 1, 0.0);
+    for (int L = sl->nlev - 1; L >= 0; --L) {
+        const int r = sl->geo.lv[L].r;
+        const double ty = std::min(2.0 * r + 1, (double)H), tx = std::min(2.0 * r + 1, (double)W);
+        sl->it_ns[L] = N * D * (tx + ty) * 4.0 / 43.0 + N * 0.06 + 15000.0;
+        sl->rem_ns[L] = sl->rem_ns[L + 1] + 53.0 * sl->it_ns[L];
+    }
+}
+
+int level_of(const Slot* sl) {
+    return std::min(std::max(sl->last.level, 0), (int)sl->it_ns.size() - 1);
+}
+
+// The grids the next batch of sweeps advances.  FIFO_FILL: admission order;
+// SHORTEST_FIRST: least estimated work left first; both take grids until the
+// estimated time of one sweep over them reaches kFillNs (a grid at a large
+// radius fills a sweep alone; grids at small radii, whose launches are too
+// short to fill the GPU, share one).  ALL: every admitted grid.
+constexpr double kFillNs = 600000.0;
+
+std::vector<Slot*> choose(plas_server* srv) {
+    std::vector<Slot*> cand;
+    for (auto& p : srv->running)
+        if (p->active && !finished(*p, srv->s)) cand.push_back(p.get());
+    if (srv->policy == PLAS_SERVE_ALL) return cand;
+    if (srv->policy == PLAS_SERVE_SHORTEST_FIRST)
+        std::stable_sort(cand.begin(), cand.end(), [](const Slot* a, const Slot* b) {
+            return a->rem_ns[level_of(a)] < b->rem_ns[level_of(b)];
+        });
+    std::vector<Slot*> run;
+    double t = 0.0;
+    for (Slot* sl : cand) {
+        run.push_back(sl);
+        t += sl->it_ns[level_of(sl)];
+        if (t >= kFillNs) break;
+    }
+    return run;
+}
+
+}  // namespace
 
 extern "C" int plas_server_create(int D, const float* weights, const plas_schedule* sched,
                                   size_t mem_budget, void* stream, plas_server** out) {
@@ -719,6 +888,15 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
     srv->st = (cudaStream_t)stream;
     srv->eng = std::make_unique<Engine>(D, srv->w, srv->s, srv->st);
     *out = srv.release();
+    return PLAS_OK;
+}
+
+extern "C" int plas_server_set_policy(plas_server* srv, int policy) {
+    set_last_error("");
+    if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
+    if (policy < PLAS_SERVE_FIFO_FILL || policy > PLAS_SERVE_ALL)
+        return fail(PLAS_ERR_INVALID_ARG, "unknown policy %d", policy);
+    srv->policy = policy;
     return PLAS_OK;
 }
 
@@ -746,12 +924,18 @@ extern "C" int plas_server_submit(plas_server* srv, const plas_job* job, long lo
     return PLAS_OK;
 }
 
+// One server step.  The host never waits for the sweeps it has just
+// enqueued: it reads the state of the previous step's batch (one batch
+// behind, as plas_sort does), so the GPU always has a batch queued while the
+// host retires, admits and chooses.
 extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap,
                                 int* n_done) {
     set_last_error("");
     if (!srv || !n_done || sweeps < 0 || cap < 0 || (cap > 0 && !done))
         return fail(PLAS_ERR_INVALID_ARG, "bad arguments");
     *n_done = 0;
+    srv->step_no += 1;
+    Engine& eng = *srv->eng;
     // admission: FIFO, while the next request fits the budget
     while (!srv->queue.empty()) {
         Slot* sl = srv->queue.front().get();
@@ -765,33 +949,71 @@ extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, i
         sl->mem = (char*)mem;
         sl->owns = true;
         srv->in_use += sl->bytes;
-        if (int e = srv->eng->admit(sl)) return e;
+        if (int e = eng.admit(sl)) return e;
+        plan_slot(sl, srv->D);
         srv->running.push_back(std::move(srv->queue.front()));
         srv->queue.pop_front();
     }
-    if (!srv->running.empty()) {
-        // grids that ended before this step's sweeps need no further work
-        if (int e = srv->eng->sweeps(sweeps > 0 ? sweeps : 1)) return e;
-        if (int e = srv->eng->poll(0)) return e;
-        if (int e = srv->eng->wait(0)) return e;
-        std::vector<Slot*> fin;
-        for (auto* sl : std::vector<Slot*>(srv->eng->active()))
-            if (finished(*sl, srv->s)) {
-                if (int e = srv->eng->retire(sl)) return e;
-                fin.push_back(sl);
+    // sweeps over the chosen grids, then a read-back of their state
+    const std::vector<Slot*> run = choose(srv);
+    eng.select(run);
+    const bool swept = !run.empty();
+    if (swept) {
+        if (int e = eng.sweeps(sweeps > 0 ? sweeps : 1)) return e;
+        if (int e = eng.poll(srv->buf)) return e;
+    }
+    // the previous read-back: retire the grids it shows finished
+    if (srv->pending) {
+        const int pb = srv->buf ^ 1;  // this step's read-back, if any, went to buf
+        if (int e = eng.wait(pb)) return e;
+        for (Slot* sl : std::vector<Slot*>(eng.polled(pb))) {
+            if (!sl->active || !finished(*sl, srv->s)) continue;
+            if (int e = eng.retire(sl)) return e;
+            cudaEvent_t ev = nullptr;
+            if (!srv->events.empty()) {
+                ev = srv->events.back();
+                srv->events.pop_back();
+            } else {
+                PLAS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             }
-        if (!fin.empty()) {
-            PLAS_CUDA(cudaStreamSynchronize(srv->st));  // outputs complete
-            for (Slot* sl : fin) {
-                if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
-                srv->completed.push_back(sl->job.ticket);
-                cudaFreeAsync(sl->mem, srv->st);
-                srv->in_use -= sl->bytes;
-                srv->running.erase(std::find_if(srv->running.begin(), srv->running.end(),
-                                                [sl](const std::unique_ptr<Slot>& p) { return p.get() == sl; }));
-            }
+            PLAS_CUDA(cudaEventRecord(ev, srv->st));
+            // stream-ordered: the memory is reused only by work queued later
+            cudaFreeAsync(sl->mem, srv->st);
+            sl->mem = nullptr;
+            srv->in_use -= sl->bytes;
+            srv->retiring.push_back({ev, sl});
         }
     }
+    srv->pending = swept;
+    if (swept) srv->buf ^= 1;
+    // completions: outputs whose copies have finished (wait only when no
+    // other work is queued, so an idle server does not spin)
+    const bool block = !swept;
+    for (size_t i = 0; i < srv->retiring.size();) {
+        auto& r = srv->retiring[i];
+        const cudaError_t q = block ? cudaEventSynchronize(r.ev) : cudaEventQuery(r.ev);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (q != cudaSuccess) return fail(PLAS_ERR_CUDA, "output copies failed: %s", cudaGetErrorString(q));
+        Slot* sl = r.sl;
+        if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
+        srv->completed.push_back(sl->job.ticket);
+        srv->events.push_back(r.ev);
+        auto it = std::find_if(srv->running.begin(), srv->running.end(),
+                               [sl](const std::unique_ptr<Slot>& p) { return p.get() == sl; });
+        srv->graveyard.emplace_back(srv->step_no, std::move(*it));
+        srv->running.erase(it);
+        srv->retiring.erase(srv->retiring.begin() + i);
+    }
+    // a finished slot can be named by at most the read-back of the step that
+    // retired it, which the next step consumes
+    srv->graveyard.erase(std::remove_if(srv->graveyard.begin(), srv->graveyard.end(),
+                                        [srv](const std::pair<long long, std::unique_ptr<Slot>>& g) {
+                                            return !srv->pending || g.first + 2 <= srv->step_no;
+                                        }),
+                         srv->graveyard.end());
     const int n = std::min<int>(cap, (int)srv->completed.size());
     for (int i = 0; i < n; ++i) done[i] = srv->completed[i];
     srv->completed.erase(srv->completed.begin(), srv->completed.begin() + n);
@@ -811,7 +1033,9 @@ extern "C" int plas_server_destroy(plas_server* srv) {
     if (!srv) return PLAS_OK;
     cudaStreamSynchronize(srv->st);
     for (auto& sl : srv->running)
-        if (sl->owns) cudaFreeAsync(sl->mem, srv->st);
+        if (sl->owns && sl->mem) cudaFreeAsync(sl->mem, srv->st);
+    for (auto& r : srv->retiring) cudaEventDestroy(r.ev);
+    for (auto e : srv->events) cudaEventDestroy(e);
     srv->eng.reset();
     cudaStreamSynchronize(srv->st);
     delete srv;

@@ -6,7 +6,8 @@
 // A pass filters the columns of a logical R x NC matrix along its rows (the
 // blur axis).  Pass 0 runs along y on the working grid (columns = (x, d);
 // output written as [x][y][d]); pass 1 runs along x on that output (columns =
-// (y, d); output = the target [y][x][d]).
+// (y, d); output = the target [y][x][d]).  The pass-0 launch also writes the
+// iteration's grouping table (one launch fewer per iteration).
 //
 // A CTA owns 128 columns and TY output rows (128 or 32, see FirTiling).  Lane l handles the four
 // columns c0+l, c0+32+l, c0+64+l, c0+96+l as two packed pairs, so each tap step
@@ -226,6 +227,20 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
             }
         }
     }
+
+    if (pass == 0) {
+        // The grouping permutation of this iteration (Sec. 3.1, one random
+        // permutation of the beta^2 block cells shared by all blocks),
+        // pi[m] for m < beta^2, spread over this grid's CTAs of the pass; the
+        // assignment launch that follows reads it.  The state is not written
+        // before that launch's schedule step.
+        const uint32_t n = (uint32_t)lv.beta * (uint32_t)lv.beta;
+        const uint32_t h = feistel_half_bits(n);
+        const uint64_t it = (uint64_t)st->it;
+        const uint32_t stride = (uint32_t)cr.count * kFirThreads;
+        for (uint32_t m = (uint32_t)cr.local * kFirThreads + threadIdx.x; m < n; m += stride)
+            gr.pi[m] = keyed_permute(m, n, h, gr.seed, kTagGroup, it);
+    }
 }
 
 int fir_ctas(int rows, int cols, int variant) {
@@ -247,6 +262,8 @@ static void fir_opt_in() {
                          (int)fir_smem<FirSmall>());
     done[dev] = true;
 }
+
+void prepare_fir_launches() { fir_opt_in(); }
 
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s) {

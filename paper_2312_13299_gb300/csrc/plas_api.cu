@@ -236,6 +236,7 @@ int plas_default_schedule(plas_schedule* out) {
     out->iters_per_poll = 8;
     out->max_iters = 0;
     out->profile = 0;
+    out->graphs = 1;
     return PLAS_OK;
 }
 

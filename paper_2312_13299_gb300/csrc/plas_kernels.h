@@ -1,5 +1,5 @@
 // plas_kernels.h -- kernels and launch wrappers of the PLAS sort (internal to
-// the CUDA library; the C ABI in plas_api.cu / batch.cu calls these).
+// the CUDA library; the C ABI in plas_api.cu / engine.cu calls these).
 //
 // Every per-iteration kernel works on a list of grids (GridRef) and reads each
 // grid's current radius level from that grid's device state, so one launch
@@ -22,7 +22,6 @@ constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
 // FIR tilings (identical results): the small-radius one below this radius
 constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1;
 constexpr int kFirSmallRadiusLimit = 24;
-constexpr int kGroupThreads = 256;
 constexpr int kAssignThreads = 256;
 
 struct Weights {
@@ -86,7 +85,6 @@ inline int target_stride(int D) { return (D + 3) & ~3; }
 
 // ---- CTA counts per grid ------------------------------------------------------
 int fir_ctas(int rows, int cols, int variant);  // rows = blur axis length, cols = cells * D
-int group_ctas(int H, int W, int num_sms);     // sized for the largest beta^2
 int assign_ctas(int H, int W, int num_sms);
 
 // ---- preparation (per grid) ----------------------------------------------------
@@ -103,8 +101,11 @@ void launch_norms(const LevelDesc* lv_dev, int nlev, int H, int W, float* table,
 
 // ---- one sweep (every grid in 'grids' advances by one iteration) --------------
 // map == nullptr: one grid (grids[0]), CTA index = blockIdx.x.
-void launch_group_table(const GridRef* grids, const CtaMap* map, int ctas, cudaStream_t s);
-// pass 0: along y (G -> H1), pass 1: along x (H1 -> T)
+// pass 0: along y (G -> H1), also writes the iteration's grouping table;
+// pass 1: along x (H1 -> T)
+// (prepare_fir_launches sets the FIR kernels' shared-memory opt-in once per
+// device; launch_fir calls it too, but a stream capture calls it first)
+void prepare_fir_launches();
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s);
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,

@@ -20,40 +20,6 @@
 namespace plas {
 
 // ============================================================================
-// grouping permutation of the block cells (Sec. 3.1, "Blockwise Linear
-// Assignment"): pi[m] for m < beta^2, fresh every iteration, shared by all
-// blocks of a grid.
-// ============================================================================
-__global__ void __launch_bounds__(kGroupThreads) group_table_kernel(
-    const GridRef* __restrict__ grids, const CtaMap* __restrict__ map) {
-    const CtaRef cr = resolve_cta(map);
-    const GridRef& gr = grids[cr.g];
-    const DevState* st = gr.st;
-    if (sweep_idle(st)) return;
-    const int beta = gr.lv[st->level].beta;
-    const uint32_t n = (uint32_t)beta * (uint32_t)beta;
-    const uint32_t h = feistel_half_bits(n);
-    const uint64_t it = (uint64_t)st->it;
-    const uint64_t seed = gr.seed;
-    uint32_t* pi = gr.pi;
-    const uint32_t stride = (uint32_t)cr.count * kGroupThreads;
-    for (uint32_t m = (uint32_t)cr.local * kGroupThreads + threadIdx.x; m < n; m += stride)
-        pi[m] = keyed_permute(m, n, h, seed, kTagGroup, it);
-}
-
-int group_ctas(int H, int W, int num_sms) {
-    const long long b = std::min(H, W);  // the largest block side
-    long long need = (b * b + kGroupThreads - 1) / kGroupThreads;
-    need = std::min<long long>(need, (long long)num_sms * 4);
-    return (int)std::max<long long>(need, 1);
-}
-
-void launch_group_table(const GridRef* grids, const CtaMap* map, int ctas, cudaStream_t s) {
-    if (ctas <= 0) return;
-    group_table_kernel<<<ctas, kGroupThreads, 0, s>>>(grids, map);
-}
-
-// ============================================================================
 // assignment (Sec. 3.1 "Blockwise Linear Assignment", Fig. "swapping_pixels"):
 // a quad of lanes per group of four cells.  Lane i loads the feature row of
 // cell p_i and the four target rows (the four lanes of a quad load the same

@@ -123,6 +123,27 @@ def test_poll_batch_size_does_not_change_result(plas):
     assert torch.equal(a, b) and torch.equal(a, c)
 
 
+def test_launch_modes_give_identical_results(plas, orc):
+    """Graph replay, direct launches and event-profiled launches run the same
+    kernels with the same arguments: the permutation and the schedule trace
+    match each other and the oracle."""
+    side = 48
+    x = synth.rgb_uniform(side, seed=6)
+    xc = _cuda(x)
+    g = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14)
+    d = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
+                  schedule=plas.Schedule(graphs=False))
+    p = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
+                  schedule=plas.Schedule(profile=True, iters_per_poll=3))
+    assert g.stats["graph_launches"] > 0 and g.stats["graph_captures"] >= 1
+    assert d.stats["graph_launches"] == 0 and p.stats["graph_launches"] == 0
+    want = orc.sort(x, side, side, seed=6)
+    for r in (g, d, p):
+        assert np.array_equal(r.perm.cpu().numpy(), want["perm"])
+        n = r.state["it"]
+        assert r.trace_S[:n].cpu().numpy().tolist() == want["trace_S"][:n].tolist()
+
+
 def _snapshot_parity(plas, orc, side, seed, radii, iters_before=2):
     """GPU runs to the first iteration of the level nearest each radius, then the
     oracle and the GPU each run one (or a few) iterations from that snapshot."""

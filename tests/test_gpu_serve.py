@@ -53,9 +53,10 @@ def test_batch_sort_d3(plas):
         assert torch.equal(got.perm, one.perm) and got.state["it"] == one.state["it"]
 
 
-def test_server_arrivals_while_running(plas):
+@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all"])
+def test_server_arrivals_while_running(plas, policy):
     reqs = _requests(seed0=10)
-    srv = plas.Server(14)
+    srv = plas.Server(14, policy=policy)
     tickets = {}
     for r in reqs[:3]:
         tickets[srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"])] = r
@@ -91,6 +92,11 @@ def test_server_budget_admission(plas):
     assert max_active >= 1
     for t, r in tickets.items():
         _same(results[t], _alone(plas, r))
+
+
+def test_server_rejects_unknown_policy(plas):
+    with pytest.raises(ValueError):
+        plas.Server(3, policy="random")
 
 
 def test_server_rejects_request_over_budget(plas):
