@@ -284,6 +284,11 @@ def run_plas(args):
     ws = torch.empty(plas.sort_workspace_bytes(side, side, D), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # launch shapes for this grid shape (the results do not depend on them)
+    t_tune = time.perf_counter()
+    tune = plas.autotune(side, side, D)
+    t_tune = time.perf_counter() - t_tune
+
     def step(profile):
         return plas.sort(x, side, side, carried=car, seed=seed, workspace=ws,
                          schedule=plas.Schedule(profile=profile), want_stats=True)
@@ -361,7 +366,10 @@ def run_plas(args):
         "config": {"workload": wl["desc"], "grid": f"{side}x{side}", "N": side * side, "D": D,
                    "carried": C, "iterations_per_sort": st0["iterations"], "levels": st0["levels"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush"},
+                   "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush",
+                   "tuning": {"fir_small_below": tune["fir_small_below"],
+                              "assign_ctas_per_sm": tune["assign_ctas_per_sm"],
+                              "autotune_s": round(t_tune, 2)}},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
@@ -526,6 +534,43 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_loss(args):
+    """Smoothness loss (Sec. 3.2) on the 1024 x 1024 x 59 grid, sigma 1, 7 x 7:
+    forward and hand-written backward, each timed with CUDA events over K
+    launches after W warm-ups (inputs 247 MB > L2).  Algorithmic bytes: the
+    forward reads x once (4 B/elem); the backward reads x and writes the
+    gradient (8 B/elem)."""
+    import torch
+    import paper_2312_13299_gb300 as plas
+    from paper_2312_13299_gb300 import synth
+    plas.load()
+    H = W = 1024
+    x = torch.from_numpy(synth.loss_grid(H, W, seed=0).astype("float32")).cuda()
+    C = x.shape[2]
+    g = torch.ones((), device="cuda")
+    peaks, psrc = _peaks()
+    out = {}
+    for name, fn, bpe in [("fwd", lambda: plas.smooth_loss_fwd(x), 4),
+                          ("bwd", lambda: plas.smooth_loss_bwd(x, g), 8)]:
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps * 10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / (args.steps * 10)
+        gbs = bpe * H * W * C / (us * 1e-6) / 1e9
+        out[name] = {"us": round(us, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peaks["hbm_gbs"], 3)}
+    line = {"metric": "smoothness loss fwd/bwd on 1024x1024x59 (sigma 1, 7x7)",
+            "value": out["bwd"]["us"], "unit": "us (backward)", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic (3DGS-shaped 14 + 45 channels)",
+            "peak_hbm_gbs": peaks["hbm_gbs"], "peak_source": psrc, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(args):
     """A bounded launch sequence for profiler captures: the workload's inputs,
     one sort capped at --ncu-case iterations (all at the top radius levels)."""
@@ -563,6 +608,8 @@ def main():
                     "(0 = the schedule's default), to profile small radii directly")
     ap.add_argument("--serve", action="store_true",
                     help="served-stream benchmark (continuous batching vs plain), own JSON line")
+    ap.add_argument("--loss", action="store_true",
+                    help="smoothness-loss fwd/bwd benchmark on 1024x1024x59, own JSON line")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
     ap.add_argument("--policies", default="fifo_fill,shortest_first,all",
@@ -574,6 +621,9 @@ def main():
         return
     if args.serve:
         run_serve(args)
+        return
+    if args.loss:
+        run_loss(args)
         return
     if args.impl == "reference":
         run_reference(args)

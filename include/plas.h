@@ -327,6 +327,45 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
                     void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* launch-shape autotuning                                                 */
+/* ---------------------------------------------------------------------- */
+/*
+ * Launch shapes the sort can choose without changing any result: the FIR
+ * tiling of the target passes (a 128-row tiling with 16 warps per CTA, or a
+ * 32-row tiling with 4 CTAs per SM; the same FMA chains either way) and the
+ * number of assignment CTAs (the residual sum is exact and order-free).  The
+ * paper has no counterpart; it is GPU plumbing.
+ *
+ * plas_autotune: times the candidates on a synthetic H x W x D grid (seeded
+ *   uniform values made on the device): both FIR tilings at radii from 1 up
+ *   to the grid's start radius, and the assignment at 2, 4, 8 and 16 CTAs
+ *   per SM at the start radius and at radius 8.  It installs the fastest
+ *   choice for sorts on this device with D channels and the nearest cell
+ *   count, and returns it with the measurements in *out.  Allocates and
+ *   frees its own device buffers on 'stream' and synchronises it.
+ *   PLAS_ERR_INVALID_ARG for unsupported sizes.
+ * plas_set_tuning: installs *t for (H, W, D) on the current device
+ *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
+ *   shape on the current device would use (the defaults 24 and 8 when
+ *   nothing is installed).  Thread-safe.
+ */
+#define PLAS_TUNE_MAX_RADII 16
+#define PLAS_TUNE_ASSIGN_CANDIDATES 4
+typedef struct plas_tuning {
+    int fir_small_below;    /* the 32-row FIR tiling for radii below this      */
+    int assign_ctas_per_sm; /* cap on assignment CTAs per SM, 1..16           */
+    int n_radii;            /* radii measured by plas_autotune                */
+    int radius[PLAS_TUNE_MAX_RADII];
+    float fir_small_us[PLAS_TUNE_MAX_RADII]; /* both passes, 32-row tiling    */
+    float fir_large_us[PLAS_TUNE_MAX_RADII]; /* both passes, 128-row tiling   */
+    int assign_per_sm[PLAS_TUNE_ASSIGN_CANDIDATES];
+    float assign_us[PLAS_TUNE_ASSIGN_CANDIDATES]; /* sum over the two radii   */
+} plas_tuning;
+int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out);
+int plas_set_tuning(int H, int W, int D, const plas_tuning* t /* host or NULL */);
+int plas_get_tuning(int H, int W, int D, plas_tuning* out);
+
+/* ---------------------------------------------------------------------- */
 /* served sorts: continuous batching under a device-memory budget          */
 /* ---------------------------------------------------------------------- */
 /*

@@ -235,6 +235,48 @@ def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] 
     return [SortResult(perm=p, carried=c, state=s.as_dict()) for (p, c), s in zip(outs, states)]
 
 
+def _tuning_dict(t: "_lib.plas_tuning") -> dict:
+    n = t.n_radii
+    return {"fir_small_below": t.fir_small_below, "assign_ctas_per_sm": t.assign_ctas_per_sm,
+            "radius": list(t.radius[:n]), "fir_small_us": [round(v, 2) for v in t.fir_small_us[:n]],
+            "fir_large_us": [round(v, 2) for v in t.fir_large_us[:n]],
+            "assign_per_sm": list(t.assign_per_sm) if n else [],
+            "assign_us": [round(v, 2) for v in t.assign_us] if n else []}
+
+
+def autotune(H: int, W: int, D: int, device=None) -> dict:
+    """Time the launch-shape candidates (FIR tiling per radius, assignment CTAs
+    per SM) on a synthetic H x W x D grid and install the fastest for sorts of
+    this shape on this device.  Results of a sort never depend on them."""
+    dev = torch.device(device) if device is not None else torch.device(
+        "cuda", torch.cuda.current_device())
+    t = _lib.plas_tuning()
+    with torch.cuda.device(dev):
+        check(load().plas_autotune(H, W, D, _stream(dev), ctypes.byref(t)), "plas_autotune")
+    return _tuning_dict(t)
+
+
+def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
+               assign_ctas_per_sm: Optional[int] = None) -> None:
+    """Install launch shapes for (H, W, D) on the current device; with both
+    arguments None the entry is removed (defaults apply again)."""
+    if fir_small_below is None and assign_ctas_per_sm is None:
+        check(load().plas_set_tuning(H, W, D, None), "plas_set_tuning")
+        return
+    cur = get_tuning(H, W, D)
+    t = _lib.plas_tuning()
+    t.fir_small_below = cur["fir_small_below"] if fir_small_below is None else fir_small_below
+    t.assign_ctas_per_sm = (cur["assign_ctas_per_sm"] if assign_ctas_per_sm is None
+                            else assign_ctas_per_sm)
+    check(load().plas_set_tuning(H, W, D, ctypes.byref(t)), "plas_set_tuning")
+
+
+def get_tuning(H: int, W: int, D: int) -> dict:
+    t = _lib.plas_tuning()
+    check(load().plas_get_tuning(H, W, D, ctypes.byref(t)), "plas_get_tuning")
+    return _tuning_dict(t)
+
+
 class Server:
     """Continuous batching of sort requests (plas_server_*): requests queue up,
     are admitted while their workspaces fit the device-memory budget, and

@@ -63,6 +63,18 @@ class plas_job(ctypes.Structure):
                 ("carried_out", c_void_p), ("state_out", ctypes.POINTER(plas_state))]
 
 
+TUNE_MAX_RADII = 16
+TUNE_ASSIGN_CANDIDATES = 4
+
+
+class plas_tuning(ctypes.Structure):
+    _fields_ = [("fir_small_below", c_int), ("assign_ctas_per_sm", c_int), ("n_radii", c_int),
+                ("radius", c_int * TUNE_MAX_RADII), ("fir_small_us", c_float * TUNE_MAX_RADII),
+                ("fir_large_us", c_float * TUNE_MAX_RADII),
+                ("assign_per_sm", c_int * TUNE_ASSIGN_CANDIDATES),
+                ("assign_us", c_float * TUNE_ASSIGN_CANDIDATES)]
+
+
 P = ctypes.POINTER
 
 # name -> (restype, argtypes); every symbol declared in include/plas.h
@@ -91,6 +103,9 @@ SIGNATURES = {
     "plas_batch_workspace_bytes": (c_size_t, [c_int, P(plas_job), c_int]),
     "plas_batch_sort": (c_int, [c_int, P(plas_job), c_int, P(c_float), P(plas_schedule),
                                 c_void_p, c_size_t, c_void_p]),
+    "plas_autotune": (c_int, [c_int, c_int, c_int, c_void_p, P(plas_tuning)]),
+    "plas_set_tuning": (c_int, [c_int, c_int, c_int, P(plas_tuning)]),
+    "plas_get_tuning": (c_int, [c_int, c_int, c_int, P(plas_tuning)]),
     "plas_server_create": (c_int, [c_int, P(c_float), P(plas_schedule), c_size_t, c_void_p,
                                    P(c_void_p)]),
     "plas_server_set_policy": (c_int, [c_void_p, c_int]),

@@ -55,6 +55,7 @@ struct Slot {
     long long N = 0;
     int nlev = 0;
     int ctas[kClsCount] = {0, 0, 0};
+    int small_below = kDefaultSmallBelow;  // FIR tiling choice (one-grid sweeps)
     bool active = false;
     DevState last{};
     long long last_it = -1;
@@ -166,9 +167,11 @@ class Engine {
         end(e0, -1);
         launches_ += 5;
         if (int e = check_launch("preparation")) return e;
+        const Tuning tu = tuning_for(H, W, D_);
+        sl->small_below = tu.small_below;
         sl->ctas[kClsFirY] = fir_ctas(H, W * D_, kFirLargeRadius);
         sl->ctas[kClsFirX] = fir_ctas(W, H * D_, kFirLargeRadius);
-        sl->ctas[kClsAssign] = assign_ctas(H, W, nsm_);
+        sl->ctas[kClsAssign] = assign_ctas(H, W, nsm_, tu.assign_per_sm);
         sl->last = init;
         sl->active = true;
         active_.push_back(sl);
@@ -196,7 +199,7 @@ class Engine {
         if (one) {
             const Slot* sl = active_[0];
             const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
-            p.var = sl->geo.lv[L].r < kFirSmallRadiusLimit ? kFirSmallRadius : kFirLargeRadius;
+            p.var = sl->geo.lv[L].r < sl->small_below ? kFirSmallRadius : kFirLargeRadius;
             p.ctas[kClsFirY] = fir_ctas(sl->job.H, sl->job.W * D_, p.var);
             p.ctas[kClsFirX] = fir_ctas(sl->job.W, sl->job.H * D_, p.var);
         }
@@ -694,6 +697,144 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
 }
 
 // ===========================================================================
+// launch-shape autotuning
+// ===========================================================================
+namespace {
+
+// Mean device time (us) of 'reps' runs of fn, after one warm-up run.
+template <class F>
+int time_us(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int reps, F fn, float* us) {
+    fn();
+    PLAS_CUDA(cudaEventRecord(a, st));
+    for (int i = 0; i < reps; ++i) fn();
+    PLAS_CUDA(cudaEventRecord(b, st));
+    PLAS_CUDA(cudaEventSynchronize(b));
+    if (int e = check_launch("autotune")) return e;
+    float ms = 0.0f;
+    PLAS_CUDA(cudaEventElapsedTime(&ms, a, b));
+    *us = ms * 1000.0f / (float)reps;
+    return PLAS_OK;
+}
+
+int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaEvent_t a,
+                 cudaEvent_t b, plas_tuning* out) {
+    plas_schedule s;
+    plas_default_schedule(&s);
+    s.graphs = 0;
+    const int rtop = std::max(1, (int)std::floor(start_radius(s, H, W)));
+    std::vector<int> radii;
+    for (int r : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512})
+        if (r <= rtop && (int)radii.size() < PLAS_TUNE_MAX_RADII - 1) radii.push_back(r);
+    if (radii.back() != rtop) radii.push_back(rtop);
+    const int assign_r[2] = {rtop, std::min(8, rtop)};
+    const int per_sm[PLAS_TUNE_ASSIGN_CANDIDATES] = {2, 4, 8, 16};
+    float assign_us[PLAS_TUNE_ASSIGN_CANDIDATES] = {0, 0, 0, 0};
+    Weights w{};
+    if (int e = make_weights(nullptr, D, &w)) return e;
+    const int nsm = num_sms();
+    constexpr int kReps = 5;
+    out->n_radii = (int)radii.size();
+    for (size_t i = 0; i < radii.size(); ++i) {
+        const int r = radii[i];
+        plas_schedule sr = s;
+        sr.phi0 = (double)r;  // level 0 has radius r
+        Engine eng(D, w, sr, st);
+        Slot sl;
+        sl.job.x = x;
+        sl.job.H = H;
+        sl.job.W = W;
+        sl.job.seed = 1;
+        sl.mem = ws;
+        if (int e = eng.admit(&sl)) return e;
+        out->radius[i] = r;
+        for (int var : {kFirLargeRadius, kFirSmallRadius}) {
+            const int c0 = fir_ctas(H, W * D, var), c1 = fir_ctas(W, H * D, var);
+            float us = 0.0f;
+            if (int e = time_us(st, a, b, kReps, [&] {
+                    launch_fir(0, sl.ws.ref, nullptr, c0, D, var, st);
+                    launch_fir(1, sl.ws.ref, nullptr, c1, D, var, st);
+                }, &us))
+                return e;
+            (var == kFirSmallRadius ? out->fir_small_us : out->fir_large_us)[i] = us;
+        }
+        for (int k = 0; k < 2; ++k) {
+            if (r != assign_r[k] || (k == 1 && assign_r[1] == assign_r[0])) continue;
+            for (int c = 0; c < PLAS_TUNE_ASSIGN_CANDIDATES; ++c) {
+                const int ctas = assign_ctas(H, W, nsm, per_sm[c]);
+                float us = 0.0f;
+                if (int e = time_us(st, a, b, kReps, [&] {
+                        launch_assign(sl.ws.ref, nullptr, ctas, D, s.tol, st);
+                    }, &us))
+                    return e;
+                assign_us[c] += us;
+            }
+        }
+    }
+    // the threshold that minimises the summed time over the measured radii
+    int best_t = 1;
+    double best_cost = -1.0;
+    for (size_t j = 0; j <= radii.size(); ++j) {
+        const int t = j < radii.size() ? radii[j] : rtop + 1;
+        double cost = 0.0;
+        for (size_t i = 0; i < radii.size(); ++i)
+            cost += radii[i] < t ? out->fir_small_us[i] : out->fir_large_us[i];
+        if (best_cost < 0.0 || cost < best_cost) {
+            best_cost = cost;
+            best_t = t;
+        }
+    }
+    int best_c = 0;
+    for (int c = 0; c < PLAS_TUNE_ASSIGN_CANDIDATES; ++c) {
+        out->assign_per_sm[c] = per_sm[c];
+        out->assign_us[c] = assign_us[c];
+        if (assign_us[c] < assign_us[best_c]) best_c = c;
+    }
+    out->fir_small_below = best_t;
+    out->assign_ctas_per_sm = per_sm[best_c];
+    Tuning tu;
+    tu.small_below = best_t;
+    tu.assign_per_sm = per_sm[best_c];
+    install_tuning(H, W, D, &tu);
+    return PLAS_OK;
+}
+
+}  // namespace
+
+extern "C" int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out) {
+    set_last_error("");
+    if (!out) return fail(PLAS_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad shape");
+    const long long N = (long long)H * W;
+    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    cudaStream_t st = (cudaStream_t)stream;
+    plas_schedule s;
+    plas_default_schedule(&s);
+    const size_t ws_bytes = sort_workspace_bytes(H, W, D, s);
+    void* x = nullptr;
+    void* ws = nullptr;
+    if (cudaMallocAsync(&x, (size_t)N * D * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync(&ws, ws_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (x) cudaFreeAsync(x, st);
+        return fail(PLAS_ERR_OOM, "autotune buffers");
+    }
+    launch_fill_uniform((float*)x, N * D, 0x7475ull, st);
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = PLAS_OK;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        rc = fail(PLAS_ERR_CUDA, "event creation failed");
+    if (rc == PLAS_OK) rc = autotune_run(H, W, D, st, (float*)x, (char*)ws, a, b, out);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(x, st);
+    cudaFreeAsync(ws, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == PLAS_OK)
+        rc = fail(PLAS_ERR_CUDA, "stream sync failed");
+    return rc;
+}
+
+// ===========================================================================
 // batched sort
 // ===========================================================================
 static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedule& s,
@@ -709,7 +850,7 @@ static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedul
         total += b;
         grids += 1;
         ctas += fir_ctas(H, W * D, kFirLargeRadius) +
-                fir_ctas(W, H * D, kFirLargeRadius) + assign_ctas(H, W, nsm);
+                fir_ctas(W, H * D, kFirLargeRadius) + assign_ctas(H, W, nsm, kAssignMaxPerSm);
     }
     if (maps_at) *maps_at = total;
     return total + Engine::map_bytes(grids, ctas);

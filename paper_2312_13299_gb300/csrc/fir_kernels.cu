@@ -20,7 +20,8 @@
 // over the zero-padded column: a zero tap or a zero sample leaves the chain
 // bit-for-bit unchanged (the accumulator starts at +0 and never becomes -0),
 // so padded and per-warp trimmed step ranges give exactly the in-range sum.
-// It is then divided by the in-range tap mass.
+// It is then divided by the in-range tap mass (correctly rounded, as the
+// IEEE division).
 #include <algorithm>
 
 #include "plas_kernels.h"
@@ -48,6 +49,19 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     unsigned long long d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
+}
+
+// a / b correctly rounded, from y = RN(1/b): q = RN(a*y) is within one ulp of
+// a/b, the remainder r = a - b*q is exact (one FMA), and RN(q + r*y) is the
+// correctly rounded quotient (Markstein's theorem, IBM J. Res. Dev. 34(1),
+// 1990) as long as nothing underflows or overflows.  Magnitudes outside
+// [2^-60, 2^60] (and zero, NaN, Inf) take the IEEE division itself.
+__device__ __forceinline__ float div_rn(float a, float b, float y) {
+    const float m = fabsf(a);
+    if (!(m >= 0x1p-60f && m <= 0x1p60f)) return __fdiv_rn(a, b);
+    const float q = __fmul_rn(a, y);
+    const float r = __fmaf_rn(-q, b, a);
+    return __fmaf_rn(r, y, q);
 }
 
 __device__ __forceinline__ void cp_async_f32(float* sdst, const float* gsrc, bool valid) {
@@ -146,9 +160,11 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
     cp_async_wait_all();
     __syncthreads();
 
-    ulonglong2 acc[X], win[X];
+    float2 acc[X][2];
+    float4 win[X];
 #pragma unroll
-    for (int i = 0; i < X; ++i) acc[i] = make_ulonglong2(0ull, 0ull);
+    for (int i = 0; i < X; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
+    const float4* fring = reinterpret_cast<const float4*>(ring);
     bool started = false;
     int ci = 0;
     for (int jc = jlo; jc < jend; jc += kFirChunk, ++ci) {
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
             if (s0 < s1) {
                 if (!started) {
 #pragma unroll
-                    for (int u = 0; u < X; ++u) win[u] = ring[((rbase + s0 + u) & RM) * 32 + lane];
+                    for (int u = 0; u < X; ++u) win[u] = fring[((rbase + s0 + u) & RM) * 32 + lane];
                     started = true;
                 }
                 for (int jb = s0; jb < s1; jb += X) {
@@ -174,19 +190,22 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
 #pragma unroll
                     for (int u = 0; u < X; u += 2) {
                         // taps of steps jb+u and jb+u+1 as two (k, k) pairs
-                        const ulonglong2 k2 = *reinterpret_cast<const ulonglong2*>(tb + (jb - jc + u));
+                        const float4 k4 = *reinterpret_cast<const float4*>(tb + (jb - jc + u));
+                        const float2 ka = make_float2(k4.x, k4.y), kb = make_float2(k4.z, k4.w);
 #pragma unroll
                         for (int i = 0; i < X; ++i) {
-                            acc[i].x = ffma2(k2.x, win[(u + i) % X].x, acc[i].x);
-                            acc[i].y = ffma2(k2.x, win[(u + i) % X].y, acc[i].y);
+                            const float4 w = win[(u + i) % X];
+                            acc[i][0] = __ffma2_rn(ka, make_float2(w.x, w.y), acc[i][0]);
+                            acc[i][1] = __ffma2_rn(ka, make_float2(w.z, w.w), acc[i][1]);
                         }
-                        win[u] = ring[(nb + u) * 32 + lane];
+                        win[u] = fring[(nb + u) * 32 + lane];
 #pragma unroll
                         for (int i = 0; i < X; ++i) {
-                            acc[i].x = ffma2(k2.y, win[(u + 1 + i) % X].x, acc[i].x);
-                            acc[i].y = ffma2(k2.y, win[(u + 1 + i) % X].y, acc[i].y);
+                            const float4 w = win[(u + 1 + i) % X];
+                            acc[i][0] = __ffma2_rn(kb, make_float2(w.x, w.y), acc[i][0]);
+                            acc[i][1] = __ffma2_rn(kb, make_float2(w.z, w.w), acc[i][1]);
                         }
-                        win[u + 1] = ring[(nb + u + 1) * 32 + lane];
+                        win[u + 1] = fring[(nb + u + 1) * 32 + lane];
                     }
                 }
             }
@@ -217,13 +236,12 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
             const int y = ylo + i;
             if (y < R) {
                 const float nrm = norm[y];
+                const float rcp = __frcp_rn(nrm);  // norms are >= 1 (the centre tap)
                 float* orow = out + (long long)y * out_row;
-                const unsigned long long v[2] = {acc[i].x, acc[i].y};
+                const float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (ok[k])
-                        orow[ooff[k]] = __fdiv_rn(
-                            __uint_as_float((unsigned)(v[k >> 1] >> (32 * (k & 1)))), nrm);
+                    if (ok[k]) orow[ooff[k]] = div_rn(v[k], nrm, rcp);
             }
         }
     }

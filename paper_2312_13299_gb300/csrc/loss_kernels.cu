@@ -6,12 +6,27 @@
 //     r = x - B x,   L = (1/M) sum lam_c r^2,   dL/dx = (2 g / M) lam_c (r - B r)
 // B is separable with zero padding and symmetric taps, so B^T = B.
 //
-// One streaming kernel evaluates v = u - B u for u = x (forward, and the first
-// backward pass) or u = r (second backward pass).  A CTA owns a strip of 32
-// cells x all C channels and walks down TYS rows: each input row segment
-// (with a halo of h cells) is loaded once, blurred along x into a ring of
-// 2h+1 rows in shared memory, and the centre row of the ring is blurred along
-// y.  Partial sums are FP64 per CTA and reduced in a fixed order.
+// One kernel evaluates v = u - B u for u = x (forward, and the first backward
+// pass) or u = r (second backward pass).
+//
+// stream_kernel (half-widths h <= 7): a thread owns one channel c of XB = 4
+// consecutive cells and walks down a band of rows, loading each row one row
+// ahead of its use.  Consecutive threads take
+// consecutive channels, so every load of a warp is one contiguous run of the
+// channel-last grid.  Each input row's XB + 2h values are loaded once and
+// blurred along x in registers into a ring of the last 2h+1 blurred rows; the
+// centre row of the ring is then blurred along y.  The row loop is unrolled by
+// 2h+1, so every ring slot is a static register.  No shared memory, no
+// barriers.
+//
+// smooth_kernel (larger h): a CTA owns a strip of 32 cells x all C channels,
+// blurs each input row along x into a ring of 2h+1 rows in shared memory and
+// the centre row along y.
+//
+// Both use the same FMA chains (ascending taps along x, then along y).  Loss
+// partial sums are FP32 over at most (2h+1) x 8 terms, then FP64 per CTA,
+// reduced in a fixed order.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -110,6 +125,281 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(
     }
 }
 
+constexpr int kXB = 4;           // cells per thread (stream_kernel)
+constexpr int kStreamThreads = 128;
+constexpr int kStreamMaxH = 7;
+
+template <int HH, bool GRAD>
+__global__ void __launch_bounds__(kStreamThreads, 8) stream_kernel(
+    const float* __restrict__ u, int H, int W, int C, int band, Taps tp,
+    const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
+    double inv_m, double* __restrict__ partials) {
+    constexpr int R = 2 * HH + 1;
+    constexpr int NV = kXB + 2 * HH;
+    const int nxb = (W + kXB - 1) / kXB;
+    const long long gid = (long long)blockIdx.x * kStreamThreads + threadIdx.x;
+    const bool live = gid < (long long)nxb * C;
+    const int c = live ? (int)(gid % C) : 0;
+    const int x0 = live ? (int)(gid / C) * kXB : 0;
+    const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);  // output rows [y0, y1)
+    const float* b = tp.b;  // kernel parameter (constant bank)
+    const float l = (lam && live) ? __ldg(lam + c) : 1.0f;
+    float coef = 0.0f;
+    if (GRAD) coef = __fmul_rn((float)(2.0 * (double)(*gscalar) * inv_m), l);
+    const long long rowstride = (long long)W * C;
+    const float* __restrict__ uc = u + c + (long long)(x0 - HH) * C;  // cell x0 - HH of row 0
+    // the loads of one input row (zero outside the grid)
+    auto load_row = [&](int yi, float* v) {
+        const bool yok = live && yi >= 0 && yi < H;
+        const float* row = uc + (long long)yi * rowstride;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const int xs = x0 - HH + k;
+            v[k] = (yok && (unsigned)xs < (unsigned)W) ? __ldg(row + k * C) : 0.0f;
+        }
+    };
+
+    float hr[R][kXB];  // x-blurred rows; row yi sits in slot (yi - ystart) mod R
+    double part = 0.0;
+    float band_acc = 0.0f;
+    const int ystart = y0 - HH, yend = y1 + HH;  // input rows [ystart, yend)
+    float vn[NV];  // the next row's values, loaded one row ahead
+    load_row(ystart, vn);
+    for (int yb = ystart; yb < yend; yb += R) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int yi = yb + q;
+            if (yi < yend) {  // uniform over the CTA
+                float v[NV];
+#pragma unroll
+                for (int k = 0; k < NV; ++k) v[k] = vn[k];
+                if (yi + 1 < yend) load_row(yi + 1, vn);
+#pragma unroll
+                for (int i = 0; i < kXB; ++i) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) acc = __fmaf_rn(b[j], v[i + j], acc);
+                    hr[q][i] = acc;
+                }
+                const int yc = yi - HH;  // the output row whose ring is now full
+                if (yc >= y0) {
+                    const float* crow = uc + (long long)yc * rowstride + HH * C;
+                    float sq = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < kXB; ++i) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < R; ++j) acc = __fmaf_rn(b[j], hr[(q + 1 + j) % R][i], acc);
+                        const int xc = x0 + i;
+                        if (live && xc < W) {
+                            const float vv = __fsub_rn(__ldg(crow + i * C), acc);
+                            const long long o = (long long)yc * rowstride + (long long)xc * C + c;
+                            if (GRAD) {
+                                out[o] = __fmul_rn(coef, vv);
+                            } else {
+                                if (out) out[o] = vv;
+                                sq = __fmaf_rn(vv, vv, sq);
+                            }
+                        }
+                    }
+                    if (!GRAD) band_acc = __fmaf_rn(l, sq, band_acc);
+                }
+            }
+        }
+        if (!GRAD) {  // at most R rows x kXB cells in one FP32 partial
+            part += (double)band_acc;
+            band_acc = 0.0f;
+        }
+    }
+    if (!GRAD) {
+        __shared__ double red[kStreamThreads / 32];
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = 0.0;
+            for (int w = 0; w < kStreamThreads / 32; ++w) s2 += red[w];
+            partials[blockIdx.y * gridDim.x + blockIdx.x] = s2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// staged_kernel (h <= 7, C <= 256): as stream_kernel, but each input row of
+// the CTA's span (cells [x0 - h, x0 + XC + h) x all C channels, one contiguous
+// run of the channel-last grid) is copied into a ring of shared-memory rows
+// by 16-byte cp.async, kSgAhead rows ahead of its use; threads then read their
+// taps and centre values from shared memory.  Rows outside the grid are
+// zero-filled by the copy; cells outside [0, W) are masked in the CTAs at the
+// grid's left and right edges only.  A thread owns kSgItems items of 4 cells x
+// 1 channel.
+// ---------------------------------------------------------------------------
+constexpr int kSgThreads = 256;
+constexpr int kSgItems = 1;
+constexpr int kSgAhead = 3;
+
+__device__ __forceinline__ void cp_async_16z(void* sdst, const void* gsrc, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int HH>
+struct SgRing {
+    static constexpr int NS = kSgAhead + HH + 2;  // a slot is rewritten only after its last reader
+};
+
+template <int HH, bool GRAD, bool EDGE>
+__device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, int W, int C,
+                                            int band, int G, int slot_f, const Taps& tp,
+                                            const float* __restrict__ lam, float* __restrict__ out,
+                                            float coef0, double* __restrict__ partials,
+                                            float* __restrict__ sg) {
+    constexpr int R = 2 * HH + 1;
+    constexpr int NV = 4 + 2 * HH;
+    constexpr int NS = SgRing<HH>::NS;
+    const int XC = 4 * G;
+    const int x0 = blockIdx.x * XC;
+    const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);
+    const long long WC = (long long)W * C, total = (long long)H * WC;
+    const int span = (XC + 2 * HH) * C;  // floats of one staged row
+    const int n4 = (span + 3 + 3) / 4;   // 16-byte chunks incl. the alignment shift
+    const int t = threadIdx.x;
+
+    // items: (cells x0 + 4g .. +3, channel c)
+    int soff[kSgItems];  // offset of the item's first tap in a staged row
+    int cc[kSgItems], xg[kSgItems];
+    bool ok[kSgItems];
+    float l[kSgItems];
+#pragma unroll
+    for (int m = 0; m < kSgItems; ++m) {
+        const int i = t + kSgThreads * m;
+        const int g = i / C;
+        cc[m] = i - g * C;
+        xg[m] = x0 + 4 * g;
+        ok[m] = g < G && xg[m] < W;
+        soff[m] = g < G ? 4 * g * C + cc[m] : 0;  // unused items read in-bounds
+        l[m] = (lam && ok[m]) ? __ldg(lam + cc[m]) : 1.0f;
+    }
+    // stage row yi into its slot; returns nothing, commits one group
+    auto stage = [&](int yi) {
+        float* dst = sg + (size_t)(((yi % NS) + NS) % NS) * slot_f;
+        const bool yok = yi >= 0 && yi < H;
+        const long long gs = (long long)yi * WC + (long long)(x0 - HH) * C;
+        const long long s0 = gs >= 0 ? (gs & ~3LL) : -(((-gs) + 3) & ~3LL);
+        for (int q = t; q < n4; q += kSgThreads) {
+            const long long p = s0 + 4LL * q;
+            int bytes = 0;
+            if (yok && p >= 0 && p < total) bytes = (int)min(16LL, 4 * (total - p));
+            cp_async_16z(dst + 4 * q, bytes ? (const void*)(u + p) : (const void*)u, bytes);
+        }
+        cp_async_commit();
+    };
+    auto row_off = [&](int yi) -> int {  // alignment shift of row yi inside its slot
+        const long long gs = (long long)yi * WC + (long long)(x0 - HH) * C;
+        return (int)(((gs % 4) + 4) % 4);
+    };
+
+    float hr[R][kSgItems][4];
+    double part = 0.0;
+    float band_acc = 0.0f;
+    const int ystart = y0 - HH, yend = y1 + HH;
+#pragma unroll
+    for (int a = 0; a < kSgAhead; ++a) stage(ystart + a);
+    for (int yb = ystart; yb < yend; yb += R) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int yi = yb + q;
+            if (yi < yend) {
+                stage(yi + kSgAhead);  // (beyond the band: zero rows, never read)
+                cp_async_wait<kSgAhead>();
+                __syncthreads();
+                const float* rx = sg + (size_t)(((yi % NS) + NS) % NS) * slot_f + row_off(yi);
+#pragma unroll
+                for (int m = 0; m < kSgItems; ++m) {
+                    float v[NV];
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) {
+                        float val = rx[soff[m] + k * C];
+                        if (EDGE) {
+                            const int xs = xg[m] - HH + k;
+                            val = (xs >= 0 && xs < W) ? val : 0.0f;
+                        }
+                        v[k] = val;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < R; ++j) acc = __fmaf_rn(tp.b[j], v[i + j], acc);
+                        hr[q][m][i] = acc;
+                    }
+                }
+                const int yc = yi - HH;
+                if (yc >= y0) {
+                    const float* rc = sg + (size_t)(((yc % NS) + NS) % NS) * slot_f + row_off(yc);
+#pragma unroll
+                    for (int m = 0; m < kSgItems; ++m) {
+                        float sq = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float acc = 0.0f;
+#pragma unroll
+                            for (int j = 0; j < R; ++j)
+                                acc = __fmaf_rn(tp.b[j], hr[(q + 1 + j) % R][m][i], acc);
+                            const int xc = xg[m] + i;
+                            if (ok[m] && xc < W) {
+                                const float vv = __fsub_rn(rc[soff[m] + (HH + i) * C], acc);
+                                const long long o = (long long)yc * WC + (long long)xc * C + cc[m];
+                                if (GRAD) {
+                                    out[o] = __fmul_rn(__fmul_rn(coef0, l[m]), vv);
+                                } else {
+                                    if (out) out[o] = vv;
+                                    sq = __fmaf_rn(vv, vv, sq);
+                                }
+                            }
+                        }
+                        if (!GRAD) band_acc = __fmaf_rn(l[m], sq, band_acc);
+                    }
+                }
+            }
+        }
+        if (!GRAD) {  // at most R rows x 2 items x 4 cells in one FP32 partial
+            part += (double)band_acc;
+            band_acc = 0.0f;
+        }
+    }
+    cp_async_wait<0>();
+    if (!GRAD) {
+        __shared__ double red[kSgThreads / 32];
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, off);
+        if ((t & 31) == 0) red[t >> 5] = part;
+        __syncthreads();
+        if (t == 0) {
+            double s2 = 0.0;
+            for (int w = 0; w < kSgThreads / 32; ++w) s2 += red[w];
+            partials[blockIdx.y * gridDim.x + blockIdx.x] = s2;
+        }
+    }
+}
+
+template <int HH, bool GRAD>
+__global__ void __launch_bounds__(kSgThreads) staged_kernel(
+    const float* __restrict__ u, int H, int W, int C, int band, int G, int slot_f, Taps tp,
+    const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
+    double inv_m, double* __restrict__ partials) {
+    extern __shared__ __align__(16) float sg[];
+    const float coef0 = GRAD ? (float)(2.0 * (double)(*gscalar) * inv_m) : 0.0f;
+    const int x0 = blockIdx.x * 4 * G;
+    if (x0 < HH || x0 + 4 * G + HH > W)
+        staged_body<HH, GRAD, true>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
+    else
+        staged_body<HH, GRAD, false>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
+}
+
 // Fixed-order sum of the per-CTA partials (one CTA, fixed tree).
 __global__ void finish_loss_kernel(const double* __restrict__ partials, int n, double inv_m,
                                    float* __restrict__ loss) {
@@ -137,7 +427,11 @@ static int check_args(const float* x, int H, int W, int C, float sigma, int ksiz
         return PLAS_ERR_INVALID_ARG;
     }
     if (!(sigma > 0.0f)) { plas::set_last_error("sigma must be > 0"); return PLAS_ERR_INVALID_ARG; }
-    if (smem_bytes(C, ksize / 2) > 200 * 1024) { plas::set_last_error("too many channels"); return PLAS_ERR_INVALID_ARG; }
+    // the shared-memory strip kernel (ksize > 15) holds 32 + 2h cells x C channels
+    if (ksize / 2 > kStreamMaxH && smem_bytes(C, ksize / 2) > 200 * 1024) {
+        plas::set_last_error("too many channels");
+        return PLAS_ERR_INVALID_ARG;
+    }
     return PLAS_OK;
 }
 
@@ -156,10 +450,22 @@ static Taps make_taps(float sigma, int ksize) {
 
 static dim3 grid_of(int H, int W) { return dim3((W + kTX - 1) / kTX, (H + kTYS - 1) / kTYS); }
 
-static size_t ws_bytes_for(int H, int W, int C) {
+// Partial sums of either kernel for any ksize (the larger of the two counts).
+static size_t partial_bytes(int H, int W, int C) {
+    const long long nthr = (long long)((W + kXB - 1) / kXB) * C;
+    const long long gx = (nthr + kStreamThreads - 1) / kStreamThreads;
+    const long long n_stream = gx * ((H + 31) / 32);
     const dim3 g = grid_of(H, W);
-    const size_t part = ((size_t)g.x * g.y * sizeof(double) + 255) / 256 * 256;
-    return part + (size_t)H * W * C * sizeof(float);
+    long long n = std::max<long long>(n_stream, (long long)g.x * g.y);
+    if (C <= kSgThreads * kSgItems) {
+        const int G = (kSgThreads * kSgItems) / C;
+        n = std::max<long long>(n, (long long)((W + 4 * G - 1) / (4 * G)) * ((H + 31) / 32));
+    }
+    return ((size_t)n * sizeof(double) + 255) / 256 * 256;
+}
+
+static size_t ws_bytes_for(int H, int W, int C) {
+    return partial_bytes(H, W, C) + (size_t)H * W * C * sizeof(float);
 }
 
 // Dynamic shared memory above 48 KB needs an opt-in; request exactly what the
@@ -169,6 +475,138 @@ static bool set_smem_attr(size_t bytes) {
     if (bytes <= 48 * 1024) return true;
     return cudaFuncSetAttribute(smooth_kernel<GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)bytes) == cudaSuccess;
+}
+
+// Launch plan of one pass: the streaming kernel for h <= 7 (band rows per CTA
+// chosen so that the grid has at most max_partials CTAs), else the
+// shared-memory strip kernel.
+struct Plan {
+    bool stream = false;
+    bool staged = false;
+    dim3 grid;
+    int band = 0;
+    int G = 0, slot_f = 0;
+    size_t smem = 0;
+    long long partials = 0;
+};
+
+constexpr size_t kSgMaxSmem = 160 * 1024;
+
+static int ring_slots(int h) { return kSgAhead + h + 2; }
+
+static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_partials) {
+    Plan p;
+    if (h <= kStreamMaxH && C <= kSgThreads * kSgItems &&
+        (reinterpret_cast<uintptr_t>(u) % 16) == 0) {
+        const int G = (kSgThreads * kSgItems) / C;
+        const int span = (4 * G + 2 * h) * C;
+        const int slot_f = ((span + 6) / 4) * 4;
+        const size_t smem = (size_t)ring_slots(h) * slot_f * sizeof(float);
+        const long long gx = (W + 4 * G - 1) / (4 * G);
+        int band = 32;
+        while (gx * ((H + band - 1) / band) > max_partials && band < H) band *= 2;
+        if (smem <= kSgMaxSmem && gx * ((H + band - 1) / band) <= max_partials) {
+            p.staged = true;
+            p.G = G;
+            p.slot_f = slot_f;
+            p.smem = smem;
+            p.band = band;
+            p.grid = dim3((unsigned)gx, (unsigned)((H + band - 1) / band));
+            p.partials = gx * ((H + band - 1) / band);
+            return p;
+        }
+    }
+    if (h <= kStreamMaxH) {
+        const long long nthr = (long long)((W + kXB - 1) / kXB) * C;
+        const long long gx = (nthr + kStreamThreads - 1) / kStreamThreads;
+        int band = 32;
+        while ((long long)gx * ((H + band - 1) / band) > max_partials && band < H) band *= 2;
+        if (gx <= 0x7fffffffLL && gx * ((H + band - 1) / band) <= max_partials) {
+            p.stream = true;
+            p.band = band;
+            p.grid = dim3((unsigned)gx, (unsigned)((H + band - 1) / band));
+            p.partials = gx * ((H + band - 1) / band);
+            return p;
+        }
+    }
+    p.grid = grid_of(H, W);
+    p.smem = smem_bytes(C, h);
+    p.partials = (long long)p.grid.x * p.grid.y;
+    return p;
+}
+
+template <int HH>
+static int launch_staged(bool grad, const Plan& p, const float* u, int H, int W, int C,
+                         const Taps& tp, const float* lam, float* out, const float* g,
+                         double inv_m, double* partials, cudaStream_t st) {
+    if (p.smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(staged_kernel<HH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.smem) != cudaSuccess ||
+            cudaFuncSetAttribute(staged_kernel<HH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.smem) != cudaSuccess)
+            return PLAS_ERR_INVALID_ARG;
+    }
+    if (grad)
+        staged_kernel<HH, true><<<p.grid, kSgThreads, p.smem, st>>>(u, H, W, C, p.band, p.G, p.slot_f,
+                                                                    tp, lam, out, g, inv_m, partials);
+    else
+        staged_kernel<HH, false><<<p.grid, kSgThreads, p.smem, st>>>(u, H, W, C, p.band, p.G, p.slot_f,
+                                                                     tp, lam, out, g, inv_m, partials);
+    return PLAS_OK;
+}
+
+template <int HH>
+static void launch_stream(bool grad, const Plan& p, const float* u, int H, int W, int C,
+                          const Taps& tp, const float* lam, float* out, const float* g,
+                          double inv_m, double* partials, cudaStream_t st) {
+    if (grad)
+        stream_kernel<HH, true><<<p.grid, kStreamThreads, 0, st>>>(u, H, W, C, p.band, tp, lam, out,
+                                                                   g, inv_m, partials);
+    else
+        stream_kernel<HH, false><<<p.grid, kStreamThreads, 0, st>>>(u, H, W, C, p.band, tp, lam,
+                                                                    out, g, inv_m, partials);
+}
+
+// v = u - B u over the grid (GRAD: out = (2 g / M) lam v; else out = v if
+// given, and the per-CTA weighted sums of v^2 into partials).
+static int run_pass(bool grad, const Plan& p, const float* u, int H, int W, int C, int h,
+                    const Taps& tp, const float* lam, float* out, const float* g, double inv_m,
+                    double* partials, cudaStream_t st) {
+    if (p.staged) {
+        switch (h) {
+            case 0: return launch_staged<0>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 1: return launch_staged<1>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 2: return launch_staged<2>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 3: return launch_staged<3>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 4: return launch_staged<4>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 5: return launch_staged<5>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 6: return launch_staged<6>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            default: return launch_staged<7>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+        }
+    }
+    if (p.stream) {
+        switch (h) {
+            case 0: launch_stream<0>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 1: launch_stream<1>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 2: launch_stream<2>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 3: launch_stream<3>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 4: launch_stream<4>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 5: launch_stream<5>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            case 6: launch_stream<6>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+            default: launch_stream<7>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
+        }
+        return PLAS_OK;
+    }
+    if (grad) {
+        if (!set_smem_attr<true>(p.smem)) return PLAS_ERR_INVALID_ARG;
+        smooth_kernel<true><<<p.grid, kThreads, p.smem, st>>>(u, H, W, C, h, tp, lam, out, g, inv_m,
+                                                              partials);
+    } else {
+        if (!set_smem_attr<false>(p.smem)) return PLAS_ERR_INVALID_ARG;
+        smooth_kernel<false><<<p.grid, kThreads, p.smem, st>>>(u, H, W, C, h, tp, lam, out, g,
+                                                               inv_m, partials);
+    }
+    return PLAS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,8 +657,9 @@ int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int k
     if (int e = check_args(x, H, W, C, sigma, ksize)) return e;
     if (!loss) { plas::set_last_error("loss is NULL"); return PLAS_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 g = grid_of(H, W);
-    const size_t need = (size_t)g.x * g.y * sizeof(double);
+    const int h = ksize / 2;
+    const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
+    const size_t need = (size_t)p.partials * sizeof(double);
     void* mem = workspace;
     if (mem) {
         if (ws_bytes < need || (reinterpret_cast<uintptr_t>(mem) % 256)) {
@@ -232,20 +671,17 @@ int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int k
         plas::set_last_error("allocation failed");
         return PLAS_ERR_OOM;
     }
-    const int h = ksize / 2;
-    const size_t sm = smem_bytes(C, h);
-    if (!set_smem_attr<false>(sm)) {
-        cudaGetLastError();
-        if (!workspace) cudaFreeAsync(mem, st);
-        plas::set_last_error("too many channels for the shared-memory tile");
-        return PLAS_ERR_INVALID_ARG;
-    }
     const double inv_m = 1.0 / ((double)H * W * C);
-    smooth_kernel<false><<<g, kThreads, sm, st>>>(x, H, W, C, h, make_taps(sigma, ksize), ch_weights,
-                                                  nullptr, nullptr, inv_m, (double*)mem);
-    finish_loss_kernel<<<1, 1024, 0, st>>>((const double*)mem, (int)(g.x * g.y), inv_m, loss);
+    int rc = run_pass(false, p, x, H, W, C, h, make_taps(sigma, ksize), ch_weights, nullptr, nullptr,
+                      inv_m, (double*)mem, st);
+    if (rc == PLAS_OK)
+        finish_loss_kernel<<<1, 1024, 0, st>>>((const double*)mem, (int)p.partials, inv_m, loss);
     cudaError_t e = cudaGetLastError();
     if (!workspace) cudaFreeAsync(mem, st);
+    if (rc != PLAS_OK) {
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return rc;
+    }
     if (e != cudaSuccess) {
         plas::set_last_error(cudaGetErrorString(e));
         return PLAS_ERR_CUDA;
@@ -259,7 +695,6 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
     if (int e = check_args(x, H, W, C, sigma, ksize)) return e;
     if (!grad_loss || !grad_x) { plas::set_last_error("grad_loss / grad_x is NULL"); return PLAS_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 g = grid_of(H, W);
     const size_t need = ws_bytes_for(H, W, C);
     void* mem = workspace;
     if (mem) {
@@ -272,26 +707,22 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
         plas::set_last_error("allocation failed");
         return PLAS_ERR_OOM;
     }
-    const size_t part = ((size_t)g.x * g.y * sizeof(double) + 255) / 256 * 256;
-    float* r = (float*)((char*)mem + part);
+    float* r = (float*)((char*)mem + partial_bytes(H, W, C));
     const int h = ksize / 2;
-    const size_t sm = smem_bytes(C, h);
-    if (!set_smem_attr<false>(sm) || !set_smem_attr<true>(sm)) {
-        cudaGetLastError();
-        if (!workspace) cudaFreeAsync(mem, st);
-        plas::set_last_error("too many channels for the shared-memory tile");
-        return PLAS_ERR_INVALID_ARG;
-    }
+    const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
     const double inv_m = 1.0 / ((double)H * W * C);
     const Taps tp = make_taps(sigma, ksize);
-    // pass 1: r = x - B x (the weighted residual sum is produced as a by-product)
-    smooth_kernel<false><<<g, kThreads, sm, st>>>(x, H, W, C, h, tp, ch_weights, r, nullptr, inv_m,
-                                                  (double*)mem);
+    // pass 1: r = x - B x (the weighted residual sums are a by-product)
+    int rc = run_pass(false, p, x, H, W, C, h, tp, ch_weights, r, nullptr, inv_m, (double*)mem, st);
     // pass 2: grad = (2 g / M) lam (r - B r)
-    smooth_kernel<true><<<g, kThreads, sm, st>>>(r, H, W, C, h, tp, ch_weights, grad_x, grad_loss,
-                                                 inv_m, nullptr);
+    if (rc == PLAS_OK)
+        rc = run_pass(true, p, r, H, W, C, h, tp, ch_weights, grad_x, grad_loss, inv_m, nullptr, st);
     cudaError_t e = cudaGetLastError();
     if (!workspace) cudaFreeAsync(mem, st);
+    if (rc != PLAS_OK) {
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return rc;
+    }
     if (e != cudaSuccess) {
         plas::set_last_error(cudaGetErrorString(e));
         return PLAS_ERR_CUDA;
@@ -317,18 +748,19 @@ int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigm
         return err;
     }
     const int h = ksize / 2;
-    const size_t sm = smem_bytes(C, h);
-    if (!set_smem_attr<false>(sm)) {
-        cudaGetLastError();
-        plas::set_last_error("too many channels for the shared-memory tile");
-        return PLAS_ERR_INVALID_ARG;
-    }
+    // taller row bands keep the CTA count (one partial each) within the array
+    const Plan p = plan_for(x, H, W, C, h, kNoAllocMaxPartials);
     cudaStream_t st = (cudaStream_t)stream;
     const double inv_m = 1.0 / ((double)H * W * C);
     // every CTA writes its own partial, so the array needs no clearing
-    smooth_kernel<false><<<g, kThreads, sm, st>>>(x, H, W, C, h, make_taps(sigma, ksize), ch_weights,
-                                                  nullptr, nullptr, inv_m, partials);
-    finish_loss_kernel<<<1, 1024, 0, st>>>(partials, (int)(g.x * g.y), inv_m, loss);
+    int rc = run_pass(false, p, x, H, W, C, h, make_taps(sigma, ksize), ch_weights, nullptr, nullptr,
+                      inv_m, partials, st);
+    if (rc != PLAS_OK) {
+        cudaGetLastError();
+        plas::set_last_error("too many channels for the shared-memory tile");
+        return rc;
+    }
+    finish_loss_kernel<<<1, 1024, 0, st>>>(partials, (int)p.partials, inv_m, loss);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         plas::set_last_error(cudaGetErrorString(e));

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -195,6 +196,52 @@ int poll_buffers(size_t bytes, void** host, cudaEvent_t* ev2) {
     return PLAS_OK;
 }
 
+// ---- launch-shape tuning table --------------------------------------------------
+namespace {
+struct TuneEntry {
+    int device, H, W, D;
+    Tuning t;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+}  // namespace
+
+Tuning tuning_for(int H, int W, int D) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const TuneEntry* best = nullptr;
+    double best_d = 0.0;
+    const double ln = std::log((double)std::max(1, H) * std::max(1, W));
+    for (const auto& e : g_tune) {
+        if (e.device != dev || e.D != D) continue;
+        const double d = std::fabs(std::log((double)e.H * e.W) - ln);
+        if (!best || d < best_d) {
+            best = &e;
+            best_d = d;
+        }
+    }
+    return best ? best->t : Tuning{};
+}
+
+void install_tuning(int H, int W, int D, const Tuning* t) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.erase(std::remove_if(g_tune.begin(), g_tune.end(),
+                                [&](const TuneEntry& e) {
+                                    return e.device == dev && e.H == H && e.W == W && e.D == D;
+                                }),
+                 g_tune.end());
+    if (t) g_tune.push_back(TuneEntry{dev, H, W, D, *t});
+}
+
 }  // namespace plas
 
 using namespace plas;
@@ -205,6 +252,34 @@ using namespace plas;
 extern "C" {
 
 int plas_version(void) { return 200; }
+
+int plas_set_tuning(int H, int W, int D, const plas_tuning* t) {
+    set_last_error("");
+    if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad shape");
+    if (!t) {
+        install_tuning(H, W, D, nullptr);
+        return PLAS_OK;
+    }
+    if (t->fir_small_below < 0 || t->assign_ctas_per_sm < 1 || t->assign_ctas_per_sm > kAssignMaxPerSm)
+        return fail(PLAS_ERR_INVALID_ARG, "fir_small_below must be >= 0, assign_ctas_per_sm 1..%d",
+                    kAssignMaxPerSm);
+    Tuning tu;
+    tu.small_below = t->fir_small_below;
+    tu.assign_per_sm = t->assign_ctas_per_sm;
+    install_tuning(H, W, D, &tu);
+    return PLAS_OK;
+}
+
+int plas_get_tuning(int H, int W, int D, plas_tuning* out) {
+    set_last_error("");
+    if (!out) return fail(PLAS_ERR_INVALID_ARG, "out is NULL");
+    if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad shape");
+    memset(out, 0, sizeof(*out));
+    const Tuning t = tuning_for(H, W, D);
+    out->fir_small_below = t.small_below;
+    out->assign_ctas_per_sm = t.assign_per_sm;
+    return PLAS_OK;
+}
 
 const char* plas_last_error(void) { return g_last_error.c_str(); }
 
@@ -309,7 +384,7 @@ int plas_target(const float* x, int H, int W, int D, const float* weights, int n
         launch_finalize_prep(ws.st, N, D, w, normalize, st);
         launch_pack(x, (int)N, D, w, normalize, ws.st, 2, perm, 0, ws.G, st);
         launch_norms(ws.lv, 1, H, W, ws.table, st);
-        const int var = g.lv[0].r < kFirSmallRadiusLimit ? kFirSmallRadius : kFirLargeRadius;
+        const int var = g.lv[0].r < tuning_for(H, W, D).small_below ? kFirSmallRadius : kFirLargeRadius;
         launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st);
         launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st);
         launch_copy_features(ws.T, (int)N, D, target_stride(D), T, st);

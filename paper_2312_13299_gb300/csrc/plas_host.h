@@ -61,6 +61,19 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
                         char* base);
 size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 
+// ---- launch-shape tuning (tune.cu) ---------------------------------------------------
+// What a sort of this shape on the current device uses: the installed entry
+// for (D, H, W), else the entry with the same D and the nearest cell count,
+// else the defaults.
+constexpr int kDefaultSmallBelow = 24;
+constexpr int kDefaultAssignPerSm = 8;
+struct Tuning {
+    int small_below = kDefaultSmallBelow;
+    int assign_per_sm = kDefaultAssignPerSm;
+};
+Tuning tuning_for(int H, int W, int D);
+void install_tuning(int H, int W, int D, const Tuning* t);  // nullptr removes
+
 // ---- pinned host staging for state polls (per host thread) ----------------------------
 int poll_buffers(size_t bytes, void** host, cudaEvent_t* ev2);
 

@@ -19,9 +19,8 @@ namespace plas {
 constexpr int kMaxD = 64;
 constexpr int kFirX = 8;       // outputs per lane and column of the FIR passes
 constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
-// FIR tilings (identical results): the small-radius one below this radius
+// FIR tilings (identical results); which one a radius uses is a tuning choice
 constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1;
-constexpr int kFirSmallRadiusLimit = 24;
 constexpr int kAssignThreads = 256;
 
 struct Weights {
@@ -85,7 +84,8 @@ inline int target_stride(int D) { return (D + 3) & ~3; }
 
 // ---- CTA counts per grid ------------------------------------------------------
 int fir_ctas(int rows, int cols, int variant);  // rows = blur axis length, cols = cells * D
-int assign_ctas(int H, int W, int num_sms);
+constexpr int kAssignMaxPerSm = 16;
+int assign_ctas(int H, int W, int num_sms, int per_sm);
 
 // ---- preparation (per grid) ----------------------------------------------------
 void launch_state_reset(DevState* st, cudaStream_t s);
@@ -123,6 +123,9 @@ void launch_neighbour_metrics(const float* g, int stride, int H, int W, int D, d
 
 // ---- errors (thread-local message behind plas_last_error) ---------------------
 void set_last_error(const char* msg);
+
+// seeded uniform [0, 1) values (Philox, tag 4), for synthetic tuning inputs
+void launch_fill_uniform(float* out, long long n, uint64_t seed, cudaStream_t s);
 
 // ---- debug / standalone --------------------------------------------------------
 void launch_keyed_permutation(uint64_t seed, uint32_t tag, uint64_t counter, uint32_t n,

@@ -225,6 +225,20 @@ void launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int n, uint32_
     philox_kernel<<<ceil_div_u(n, 256), 256, 0, s>>>(ctr, k0, k1, n, out);
 }
 
+__global__ void fill_uniform_kernel(float* __restrict__ out, long long n, uint32_t k0,
+                                    uint32_t k1) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)i, 4u << 8, (uint32_t)(i >> 32), 0u), k0, k1);
+    out[i] = (float)(o.x >> 8) * (1.0f / 16777216.0f);
+}
+
+void launch_fill_uniform(float* out, long long n, uint64_t seed, cudaStream_t s) {
+    if (n <= 0) return;
+    fill_uniform_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, (uint32_t)seed,
+                                                                    (uint32_t)(seed >> 32));
+}
+
 // ============================================================================
 // outputs (Sec. 3: every attribute plane follows the one permutation)
 // ============================================================================

@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     block_shift(gr.seed, st->epoch, beta, H, W, &dy, &dx);
     const int nby = (H - dy) / beta, nbx = (W - dx) / beta;
     const int ngroups = (beta * beta) / 4;
-    const long long ngt = (long long)nby * nbx * ngroups;
+    // N <= 2^26 (checked on the host), so every cell and group index fits 32 bits
+    const int ngt = nby * nbx * ngroups;
     const double scale = ldexp(1.0, st->scale_exp);
     float* __restrict__ G = gr.G;
     const float* __restrict__ T = gr.T;
@@ -163,24 +164,24 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     unsigned long long part = 0ull;
 
     const int lane = threadIdx.x & 31, qi = lane & 3, qbase = lane & ~3;
-    const long long gwarp = ((long long)cr.local * kAssignThreads + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)cr.count * kAssignThreads) >> 5;
+    const int gwarp = (cr.local * kAssignThreads + (int)threadIdx.x) >> 5;
+    const int nwarps = (cr.count * kAssignThreads) >> 5;
     constexpr Perm24 kPerm24 = make_perm24();
     // ---- groups: 8 per warp ----
     // the grouping-table entries of the next iteration are read one iteration
     // ahead, so each iteration waits for one memory round trip, not two
-    auto group_of = [&](long long b) -> int {
-        const long long t = b + (lane >> 2);
-        return t < ngt ? (int)(t % ngroups) : 0;
+    auto group_of = [&](int b) -> int {
+        const int t = b + (lane >> 2);
+        return t < ngt ? (int)((uint32_t)t % (uint32_t)ngroups) : 0;
     };
     uint4 l4_next = make_uint4(0u, 0u, 0u, 0u);
     if (gwarp * 8 < ngt) l4_next = __ldg(reinterpret_cast<const uint4*>(pi) + group_of(gwarp * 8));
-    for (long long base = gwarp * 8; base < ngt; base += nwarps * 8) {
-        const long long task0 = base + (lane >> 2);
+    for (int base = gwarp * 8; base < ngt; base += nwarps * 8) {
+        const int task0 = base + (lane >> 2);
         const bool active = task0 < ngt;
-        const long long task = active ? task0 : 0;
-        const long long blk = task / ngroups;
-        const int by = (int)(blk / nbx), bx = (int)(blk - (long long)by * nbx);
+        const uint32_t task = active ? (uint32_t)task0 : 0u;
+        const uint32_t blk = task / (uint32_t)ngroups;
+        const int by = (int)(blk / (uint32_t)nbx), bx = (int)(blk - (uint32_t)by * (uint32_t)nbx);
         const int oy = dy + by * beta, ox = dx + bx * beta;
         const uint4 l4 = l4_next;
         if (base + nwarps * 8 < ngt)
@@ -240,14 +241,26 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
         }
     }
 
-    // ---- cells outside the full blocks ----
+    // ---- cells outside the full blocks (enumerated directly: the rows above
+    // and below the covered band, then the left and right margins of it) ----
     const int cy0 = dy, cy1 = dy + nby * beta, cx0 = dx, cx1 = dx + nbx * beta;
-    const long long N = (long long)H * W;
-    const long long gthread = (long long)cr.local * kAssignThreads + threadIdx.x;
-    const long long nthreads = (long long)cr.count * kAssignThreads;
-    for (long long p = gthread; p < N; p += nthreads) {
-        const int y = (int)(p / W), x = (int)(p - (long long)y * W);
-        if (y >= cy0 && y < cy1 && x >= cx0 && x < cx1) continue;
+    const int gthread = cr.local * kAssignThreads + (int)threadIdx.x;
+    const int nthreads = cr.count * kAssignThreads;
+    const int n_top = cy0 * W, n_bot = (H - cy1) * W, margin = W - (cx1 - cx0);
+    const int n_unc = n_top + n_bot + (cy1 - cy0) * margin;
+    for (int e = gthread; e < n_unc; e += nthreads) {
+        int y, x;
+        if (e < n_top + n_bot) {
+            const int f = e < n_top ? e : e - n_top + cy1 * W;
+            y = (int)((uint32_t)f / (uint32_t)W);
+            x = f - y * W;
+        } else {
+            const int f = e - n_top - n_bot;
+            const int row = (int)((uint32_t)f / (uint32_t)margin), c = f - row * margin;
+            y = cy0 + row;
+            x = c < cx0 ? c : cx1 + (c - cx0);
+        }
+        const int p = y * W + x;
         float grow[GS], trow[TS];
         load_row4_rw<GS / 4>(G + (size_t)p * GS, grow);
         load_row4<TS / 4>(T + (size_t)p * TS, trow);
@@ -255,14 +268,14 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     }
     // ---- leftover cells of each block (beta^2 mod 4 of them) ----
     const int nleft = beta * beta - 4 * ngroups;
-    const long long nl = (long long)nby * nbx * nleft;
-    for (long long e = gthread; e < nl; e += nthreads) {
-        const long long blk = e / nleft;
-        const int m = 4 * ngroups + (int)(e - blk * nleft);
-        const int by = (int)(blk / nbx), bx = (int)(blk - (long long)by * nbx);
+    const int nl = nby * nbx * nleft;
+    for (int e = gthread; e < nl; e += nthreads) {
+        const int blk = (int)((uint32_t)e / (uint32_t)nleft);
+        const int m = 4 * ngroups + (e - blk * nleft);
+        const int by = (int)((uint32_t)blk / (uint32_t)nbx), bx = blk - by * nbx;
         const uint32_t l = pi[m];
         const int ly = (int)(l / (uint32_t)beta), lx = (int)(l - (uint32_t)ly * (uint32_t)beta);
-        const long long p = (long long)(dy + by * beta + ly) * W + (dx + bx * beta + lx);
+        const int p = (dy + by * beta + ly) * W + (dx + bx * beta + lx);
         float grow[GS], trow[TS];
         load_row4_rw<GS / 4>(G + (size_t)p * GS, grow);
         load_row4<TS / 4>(T + (size_t)p * TS, trow);
@@ -285,16 +298,17 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
             const LevelDesc& lv = gr.lv[st->level];
             const double fy = pass_taps(H, lv.ry) * (double)W * D;
             const double fx = pass_taps(W, lv.rx) * (double)H * D;
-            schedule_step(st, N, nby, nbx, ngroups, gr.nlev, tol, gr.trace_S, gr.trace_level,
+            schedule_step(st, (long long)H * W, nby, nbx, ngroups, gr.nlev, tol, gr.trace_S, gr.trace_level,
                           gr.trace_cap, fy, fx, (double)beta * beta);
         }
     }
 }
 
-int assign_ctas(int H, int W, int num_sms) {
+int assign_ctas(int H, int W, int num_sms, int per_sm) {
     const long long N = (long long)H * W;
     long long need = (N / 4 + 63) / 64;  // one quad per group, 64 groups per CTA
-    need = std::min<long long>(need, (long long)num_sms * 8);
+    per_sm = std::min(std::max(per_sm, 1), kAssignMaxPerSm);
+    need = std::min<long long>(need, (long long)num_sms * per_sm);
     return (int)std::max<long long>(need, 1);
 }
 

@@ -41,3 +41,21 @@ def test_library_is_sm103a_only():
     from paper_2312_13299_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
     assert "-fmad=false" in build.NVFLAGS
+
+
+def test_tuning_table_round_trip_host_only():
+    """The launch-shape table is host state: install, look up (nearest cell
+    count for the same D), validate and remove -- no device work."""
+    import paper_2312_13299_gb300 as plas
+    plas.set_tuning(64, 64, 5, fir_small_below=7, assign_ctas_per_sm=3)
+    try:
+        t = plas.get_tuning(64, 64, 5)
+        assert (t["fir_small_below"], t["assign_ctas_per_sm"]) == (7, 3)
+        assert plas.get_tuning(70, 60, 5)["fir_small_below"] == 7   # nearest entry, same D
+        assert plas.get_tuning(64, 64, 6)["fir_small_below"] == 24  # other D: defaults
+        import pytest
+        with pytest.raises(RuntimeError):
+            plas.set_tuning(64, 64, 5, assign_ctas_per_sm=17)
+    finally:
+        plas.set_tuning(64, 64, 5)
+    assert plas.get_tuning(64, 64, 5)["assign_ctas_per_sm"] == 8

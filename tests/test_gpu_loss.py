@@ -61,3 +61,41 @@ def test_loss_deterministic(plas):
     a = plas.smooth_loss_fwd(x)
     b = plas.smooth_loss_fwd(x)
     assert torch.equal(a, b)
+
+
+def test_loss_in_training_loop_with_resorts(plas, orc):
+    """The smoothness loss inside an Adam loop that re-sorts the grid every 100
+    steps (Sec. 3.2 with the sort of Sec. 3.1 between steps): at every re-sort
+    the GPU loss and gradient agree with the FP64 oracle, every attribute and
+    both Adam moments follow the one permutation, and the loss falls."""
+    H = W = 64
+    x, c = synth.gaussians_3dgs(H * W, seed=3)
+    grid = np.concatenate([x, c], axis=1).astype(np.float32)  # 14 sort + 45 carried
+    P = torch.from_numpy(grid).cuda().requires_grad_(True)
+    opt = torch.optim.Adam([P], lr=1e-3)
+    losses = []
+    for step in range(300):
+        if step % 100 == 0:
+            with torch.no_grad():
+                r = plas.sort(P[:, :14].contiguous(), H, W, seed=step,
+                              schedule=plas.Schedule(shuffle_init=False))
+                st = opt.state[P] if P in opt.state else None
+                before = {k: v.clone() for k, v in st.items() if torch.is_tensor(v) and v.dim() == 2} if st else {}
+                P.copy_(plas.gather_rows(P.detach(), r.perm))
+                for k, v in before.items():
+                    st[k].copy_(plas.gather_rows(v, r.perm))
+                    assert torch.equal(st[k], v[r.perm.long()])
+            p_np = P.detach().cpu().numpy().reshape(H, W, -1).astype(np.float64)
+            L64, g64 = orc.smooth_loss64(p_np, 1.0, 7, None, grad_loss=1.0)
+            Pg = P.detach().clone().reshape(H, W, -1).requires_grad_(True)
+            L = plas.smooth_loss(Pg, 1.0, 7)
+            L.backward()
+            assert abs(L.item() - L64) <= 1e-5 * abs(L64)
+            gg = Pg.grad.cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(gg - g64) <= 1e-5 * np.linalg.norm(g64)
+        opt.zero_grad()
+        loss = plas.smooth_loss(P.reshape(H, W, -1), 1.0, 7)
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert losses[-1] < losses[0]

@@ -56,6 +56,25 @@ def test_target_bitexact(plas, orc, H, W, D, phi):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("phi", [1.0, 6.0, 40.0])
+def test_target_bitexact_wide_magnitudes(plas, orc, phi):
+    """Unnormalised values spread over 2^-80 .. 2^80 (with zeros and both
+    signs): the border-norm division is correctly rounded everywhere, on the
+    reciprocal path and on the IEEE-division path for extreme magnitudes."""
+    H, W, D = 96, 88, 3
+    rng = np.random.default_rng(int(phi * 10))
+    # exponent rising from -100 to +100 down the rows (identity placement), so
+    # that tiny, ordinary and huge accumulators all occur
+    e = np.linspace(-100, 100, H)[:, None, None] + rng.uniform(-4, 4, (H, W, D))
+    sign = np.where(rng.random((H, W, D)) < 0.3, -1.0, 1.0)
+    x = (np.exp2(e) * sign).astype(np.float32).reshape(H * W, D)
+    x[rng.random((H * W, D)) < 0.05] = 0.0
+    perm = np.arange(H * W, dtype=np.int32)
+    got = plas.target(_cuda(x), H, W, _cuda(perm), phi, normalize=False).cpu().numpy()
+    want = orc.target(x, H, W, perm, phi, normalize_=False)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
 def _sched(plas, **kw):
     return plas.Schedule(**kw)
 
@@ -142,6 +161,30 @@ def test_launch_modes_give_identical_results(plas, orc):
         assert np.array_equal(r.perm.cpu().numpy(), want["perm"])
         n = r.state["it"]
         assert r.trace_S[:n].cpu().numpy().tolist() == want["trace_S"][:n].tolist()
+
+
+def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
+    """The tuner measures both FIR tilings and four assignment grid sizes; any
+    installed choice (always 128-row, always 32-row, 1 or 16 assignment CTAs
+    per SM) gives the oracle's permutation and schedule trace."""
+    H, W, D = 72, 56, 5
+    t = plas.autotune(H, W, D)
+    assert t["radius"][0] == 1 and len(t["fir_small_us"]) == len(t["radius"])
+    assert all(v > 0 for v in t["fir_small_us"] + t["fir_large_us"] + t["assign_us"])
+    assert t["assign_ctas_per_sm"] in t["assign_per_sm"]
+    rng = np.random.default_rng(11)
+    x = rng.random((H * W, D), dtype=np.float32)
+    want = orc.sort(x, H, W, seed=11)
+    xc = _cuda(x)
+    try:
+        for small_below, per_sm in [(0, 1), (10 ** 6, 16), (t["fir_small_below"], 4)]:
+            plas.set_tuning(H, W, D, fir_small_below=small_below, assign_ctas_per_sm=per_sm)
+            got = plas.sort(xc, H, W, seed=11, trace_cap=1 << 14)
+            assert np.array_equal(got.perm.cpu().numpy(), want["perm"]), (small_below, per_sm)
+            n = got.state["it"]
+            assert got.trace_S[:n].cpu().numpy().tolist() == want["trace_S"][:n].tolist()
+    finally:
+        plas.set_tuning(H, W, D)
 
 
 def _snapshot_parity(plas, orc, side, seed, radii, iters_before=2):
