@@ -225,17 +225,19 @@ __global__ void __launch_bounds__(kStreamThreads, 8) stream_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// staged_kernel (h <= 7, C <= 256): as stream_kernel, but each input row of
-// the CTA's span (cells [x0 - h, x0 + XC + h) x all C channels, one contiguous
-// run of the channel-last grid) is copied into a ring of shared-memory rows
-// by 16-byte cp.async, kSgAhead rows ahead of its use; threads then read their
-// taps and centre values from shared memory.  Rows outside the grid are
-// zero-filled by the copy; cells outside [0, W) are masked in the CTAs at the
-// grid's left and right edges only.  A thread owns kSgItems items of 4 cells x
-// 1 channel.
+// staged_kernel (h <= 7, C <= 256): each input row of the CTA's span (cells
+// [x0 - h, x0 + XC + h) x all C channels, one contiguous run of the
+// channel-last grid) is copied into a ring of shared-memory rows by 16-byte
+// cp.async, kSgAhead rows ahead of its use.  A thread owns one channel c of 8
+// consecutive cells: it reads its 8 + 2h taps of the row from shared memory,
+// blurs them along x into a register ring of the last 2h+1 rows and blurs
+// the ring's centre row along y.  Cells are processed as pairs (i, i + 4), so
+// both passes run as packed FMAs (two IEEE FMAs per instruction: the same
+// chains as scalar FMAs).  Cells outside [0, W) and rows outside the grid
+// are zero-filled by the copy itself.
 // ---------------------------------------------------------------------------
 constexpr int kSgThreads = 256;
-constexpr int kSgItems = 1;
+constexpr int kSgCells = 8;
 constexpr int kSgAhead = 3;
 
 __device__ __forceinline__ void cp_async_16z(void* sdst, const void* gsrc, int bytes) {
@@ -243,133 +245,152 @@ __device__ __forceinline__ void cp_async_16z(void* sdst, const void* gsrc, int b
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async_4z(void* sdst, const void* gsrc, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <int HH>
-struct SgRing {
-    static constexpr int NS = kSgAhead + HH + 2;  // a slot is rewritten only after its last reader
-};
+// ring slots: a slot is rewritten only after the rows read in the previous
+// iteration (the blurred row and the centre row h rows above it)
+__host__ __device__ constexpr int sg_slots(int h) { return kSgAhead + h + 2; }
 
-template <int HH, bool GRAD, bool EDGE>
+template <int HH, bool GRAD>
 __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, int W, int C,
                                             int band, int G, int slot_f, const Taps& tp,
                                             const float* __restrict__ lam, float* __restrict__ out,
                                             float coef0, double* __restrict__ partials,
                                             float* __restrict__ sg) {
     constexpr int R = 2 * HH + 1;
-    constexpr int NV = 4 + 2 * HH;
-    constexpr int NS = SgRing<HH>::NS;
-    const int XC = 4 * G;
+    constexpr int NS = sg_slots(HH);
+    constexpr int NP = kSgCells / 2;
+    const int XC = kSgCells * G;
     const int x0 = blockIdx.x * XC;
     const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);
-    const long long WC = (long long)W * C, total = (long long)H * WC;
-    const int span = (XC + 2 * HH) * C;  // floats of one staged row
-    const int n4 = (span + 3 + 3) / 4;   // 16-byte chunks incl. the alignment shift
+    const long long WC = (long long)W * C;
+    const int span = (XC + 2 * HH) * C;
+    const int n4 = (span + 6) / 4;  // 16-byte chunks incl. the alignment shift
     const int t = threadIdx.x;
 
-    // items: (cells x0 + 4g .. +3, channel c)
-    int soff[kSgItems];  // offset of the item's first tap in a staged row
-    int cc[kSgItems], xg[kSgItems];
-    bool ok[kSgItems];
-    float l[kSgItems];
+    const int g = t / C;
+    const int c = t - g * C;
+    const int xg = x0 + kSgCells * g;
+    const bool ok = g < G && xg < W;
+    const int soff = ok ? kSgCells * g * C + c : 0;  // unused threads read in-bounds
+    const float l = (lam && ok) ? __ldg(lam + c) : 1.0f;
+    const float2 coef2 = GRAD ? make_float2(__fmul_rn(coef0, l), __fmul_rn(coef0, l))
+                              : make_float2(0.0f, 0.0f);
+    float2 b2[R];
 #pragma unroll
-    for (int m = 0; m < kSgItems; ++m) {
-        const int i = t + kSgThreads * m;
-        const int g = i / C;
-        cc[m] = i - g * C;
-        xg[m] = x0 + 4 * g;
-        ok[m] = g < G && xg[m] < W;
-        soff[m] = g < G ? 4 * g * C + cc[m] : 0;  // unused items read in-bounds
-        l[m] = (lam && ok[m]) ? __ldg(lam + cc[m]) : 1.0f;
-    }
-    // stage row yi into its slot; returns nothing, commits one group
-    auto stage = [&](int yi) {
-        float* dst = sg + (size_t)(((yi % NS) + NS) % NS) * slot_f;
-        const bool yok = yi >= 0 && yi < H;
-        const long long gs = (long long)yi * WC + (long long)(x0 - HH) * C;
-        const long long s0 = gs >= 0 ? (gs & ~3LL) : -(((-gs) + 3) & ~3LL);
+    for (int j = 0; j < R; ++j) b2[j] = make_float2(tp.b[j], tp.b[j]);
+
+    const int ystart = y0 - HH, yend = y1 + HH;
+    const int wc4 = (int)(WC & 3);
+    // staging cursor: the next row to copy, its slot and its first flat index
+    int st_row = ystart, st_slot = 0;
+    long long st_gs = (long long)ystart * WC + (long long)(x0 - HH) * C;
+    // Only the row's own cells [row0, row1) are copied; everything else
+    // (cells outside [0, W), rows outside the grid) lands as zeros.  A chunk
+    // that straddles a row boundary (only when W*C is not a multiple of 4) is
+    // copied float by float.
+    auto stage = [&]() {
+        float* dst = sg + (size_t)st_slot * slot_f;
+        const bool yok = st_row >= 0 && st_row < H;
+        const long long row0 = yok ? (long long)st_row * WC : 0, row1 = yok ? row0 + WC : 0;
+        const long long s0 = st_gs & ~3LL;  // floor to a 16-byte boundary
         for (int q = t; q < n4; q += kSgThreads) {
             const long long p = s0 + 4LL * q;
-            int bytes = 0;
-            if (yok && p >= 0 && p < total) bytes = (int)min(16LL, 4 * (total - p));
-            cp_async_16z(dst + 4 * q, bytes ? (const void*)(u + p) : (const void*)u, bytes);
+            if (p >= row0 && p + 4 <= row1) {
+                cp_async_16z(dst + 4 * q, u + p, 16);
+            } else if (p + 4 <= row0 || p >= row1) {
+                cp_async_16z(dst + 4 * q, u, 0);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool in = p + e >= row0 && p + e < row1;
+                    cp_async_4z(dst + 4 * q + e, in ? (const void*)(u + p + e) : (const void*)u, in ? 4 : 0);
+                }
+            }
         }
         cp_async_commit();
+        ++st_row;
+        st_slot = st_slot + 1 == NS ? 0 : st_slot + 1;
+        st_gs += WC;
     };
-    auto row_off = [&](int yi) -> int {  // alignment shift of row yi inside its slot
-        const long long gs = (long long)yi * WC + (long long)(x0 - HH) * C;
-        return (int)(((gs % 4) + 4) % 4);
-    };
+    // read cursors: row yi (x pass) and row yi - HH (centre)
+    int x_slot = 0, x_off = (int)(((long long)ystart * WC + (long long)(x0 - HH) * C) & 3);
+    int c_slot = NS - HH, c_off = (int)(((long long)(ystart - HH) * WC + (long long)(x0 - HH) * C) & 3);
 
-    float hr[R][kSgItems][4];
+    // cells are processed as pairs (i, i + 4), i < 4, so both passes run as
+    // packed FMAs (two IEEE FMAs per instruction, the same chains as scalar)
+    float2 hr[R][NP];  // x-blurred rows; row yi in slot (yi - ystart) mod R
     double part = 0.0;
-    float band_acc = 0.0f;
-    const int ystart = y0 - HH, yend = y1 + HH;
+    float2 band_acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int a = 0; a < kSgAhead; ++a) stage(ystart + a);
+    for (int a = 0; a < kSgAhead; ++a) stage();
     for (int yb = ystart; yb < yend; yb += R) {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int yi = yb + q;
-            if (yi < yend) {
-                stage(yi + kSgAhead);  // (beyond the band: zero rows, never read)
+            if (yi < yend) {  // uniform over the CTA
+                stage();      // row yi + kSgAhead (past the band: copied, never read)
                 cp_async_wait<kSgAhead>();
                 __syncthreads();
-                const float* rx = sg + (size_t)(((yi % NS) + NS) % NS) * slot_f + row_off(yi);
+                const float* rx = sg + (size_t)x_slot * slot_f + x_off + soff;
+                float2 v2[NP + 2 * HH];  // (tap k, tap k + 4)
 #pragma unroll
-                for (int m = 0; m < kSgItems; ++m) {
-                    float v[NV];
+                for (int k = 0; k < NP + 2 * HH; ++k) v2[k] = make_float2(rx[k * C], rx[(k + NP) * C]);
 #pragma unroll
-                    for (int k = 0; k < NV; ++k) {
-                        float val = rx[soff[m] + k * C];
-                        if (EDGE) {
-                            const int xs = xg[m] - HH + k;
-                            val = (xs >= 0 && xs < W) ? val : 0.0f;
-                        }
-                        v[k] = val;
-                    }
+                for (int i = 0; i < NP; ++i) {
+                    float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float acc = 0.0f;
-#pragma unroll
-                        for (int j = 0; j < R; ++j) acc = __fmaf_rn(tp.b[j], v[i + j], acc);
-                        hr[q][m][i] = acc;
-                    }
+                    for (int j = 0; j < R; ++j) acc = __ffma2_rn(b2[j], v2[i + j], acc);
+                    hr[q][i] = acc;
                 }
                 const int yc = yi - HH;
                 if (yc >= y0) {
-                    const float* rc = sg + (size_t)(((yc % NS) + NS) % NS) * slot_f + row_off(yc);
+                    const float* rc = sg + (size_t)c_slot * slot_f + c_off + soff + HH * C;
+                    float2 sq = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int m = 0; m < kSgItems; ++m) {
-                        float sq = 0.0f;
+                    for (int i = 0; i < NP; ++i) {
+                        float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float acc = 0.0f;
-#pragma unroll
-                            for (int j = 0; j < R; ++j)
-                                acc = __fmaf_rn(tp.b[j], hr[(q + 1 + j) % R][m][i], acc);
-                            const int xc = xg[m] + i;
-                            if (ok[m] && xc < W) {
-                                const float vv = __fsub_rn(rc[soff[m] + (HH + i) * C], acc);
-                                const long long o = (long long)yc * WC + (long long)xc * C + cc[m];
-                                if (GRAD) {
-                                    out[o] = __fmul_rn(__fmul_rn(coef0, l[m]), vv);
-                                } else {
-                                    if (out) out[o] = vv;
-                                    sq = __fmaf_rn(vv, vv, sq);
+                        for (int j = 0; j < R; ++j) acc = __ffma2_rn(b2[j], hr[(q + 1 + j) % R][i], acc);
+                        // centre - blur, one rounding (FMA with -1)
+                        const float2 vv = __ffma2_rn(make_float2(-1.0f, -1.0f), acc,
+                                                     make_float2(rc[i * C], rc[(i + NP) * C]));
+                        if (ok) {
+                            const int xa = xg + i, xb = xg + i + NP;
+                            const long long o = (long long)yc * WC + (long long)xa * C + c;
+                            if (GRAD) {
+                                const float2 gv = __fmul2_rn(coef2, vv);
+                                if (xa < W) out[o] = gv.x;
+                                if (xb < W) out[o + NP * C] = gv.y;
+                            } else {
+                                if (out) {
+                                    if (xa < W) out[o] = vv.x;
+                                    if (xb < W) out[o + NP * C] = vv.y;
                                 }
+                                const float2 m2 = make_float2(xa < W ? vv.x : 0.0f, xb < W ? vv.y : 0.0f);
+                                sq = __ffma2_rn(m2, m2, sq);
                             }
                         }
-                        if (!GRAD) band_acc = __fmaf_rn(l[m], sq, band_acc);
                     }
+                    if (!GRAD) band_acc = __ffma2_rn(make_float2(l, l), sq, band_acc);
                 }
+                // advance the read cursors
+                x_slot = x_slot + 1 == NS ? 0 : x_slot + 1;
+                x_off = (x_off + wc4) & 3;
+                c_slot = c_slot + 1 == NS ? 0 : c_slot + 1;
+                c_off = (c_off + wc4) & 3;
             }
         }
-        if (!GRAD) {  // at most R rows x 2 items x 4 cells in one FP32 partial
-            part += (double)band_acc;
-            band_acc = 0.0f;
+        if (!GRAD) {  // at most R rows x 4 cells in each FP32 partial
+            part += (double)band_acc.x + (double)band_acc.y;
+            band_acc = make_float2(0.0f, 0.0f);
         }
     }
     cp_async_wait<0>();
@@ -393,11 +414,7 @@ __global__ void __launch_bounds__(kSgThreads) staged_kernel(
     double inv_m, double* __restrict__ partials) {
     extern __shared__ __align__(16) float sg[];
     const float coef0 = GRAD ? (float)(2.0 * (double)(*gscalar) * inv_m) : 0.0f;
-    const int x0 = blockIdx.x * 4 * G;
-    if (x0 < HH || x0 + 4 * G + HH > W)
-        staged_body<HH, GRAD, true>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
-    else
-        staged_body<HH, GRAD, false>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
+    staged_body<HH, GRAD>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
 }
 
 // Fixed-order sum of the per-CTA partials (one CTA, fixed tree).
@@ -457,9 +474,9 @@ static size_t partial_bytes(int H, int W, int C) {
     const long long n_stream = gx * ((H + 31) / 32);
     const dim3 g = grid_of(H, W);
     long long n = std::max<long long>(n_stream, (long long)g.x * g.y);
-    if (C <= kSgThreads * kSgItems) {
-        const int G = (kSgThreads * kSgItems) / C;
-        n = std::max<long long>(n, (long long)((W + 4 * G - 1) / (4 * G)) * ((H + 31) / 32));
+    if (C <= kSgThreads) {
+        const int G = kSgThreads / C;
+        n = std::max<long long>(n, (long long)((W + kSgCells * G - 1) / (kSgCells * G)) * ((H + 31) / 32));
     }
     return ((size_t)n * sizeof(double) + 255) / 256 * 256;
 }
@@ -492,17 +509,15 @@ struct Plan {
 
 constexpr size_t kSgMaxSmem = 160 * 1024;
 
-static int ring_slots(int h) { return kSgAhead + h + 2; }
 
 static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_partials) {
     Plan p;
-    if (h <= kStreamMaxH && C <= kSgThreads * kSgItems &&
-        (reinterpret_cast<uintptr_t>(u) % 16) == 0) {
-        const int G = (kSgThreads * kSgItems) / C;
-        const int span = (4 * G + 2 * h) * C;
+    if (h <= kStreamMaxH && C <= kSgThreads && (reinterpret_cast<uintptr_t>(u) % 16) == 0) {
+        const int G = kSgThreads / C;
+        const int span = (kSgCells * G + 2 * h) * C;
         const int slot_f = ((span + 6) / 4) * 4;
-        const size_t smem = (size_t)ring_slots(h) * slot_f * sizeof(float);
-        const long long gx = (W + 4 * G - 1) / (4 * G);
+        const size_t smem = (size_t)sg_slots(h) * slot_f * sizeof(float);
+        const long long gx = (W + kSgCells * G - 1) / (kSgCells * G);
         int band = 32;
         while (gx * ((H + band - 1) / band) > max_partials && band < H) band *= 2;
         if (smem <= kSgMaxSmem && gx * ((H + band - 1) / band) <= max_partials) {
