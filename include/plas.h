@@ -154,7 +154,9 @@ size_t plas_sort_workspace_bytes(int H, int W, int D);
  *
  *   x            device, N x D float32: the sort features of each Gaussian
  *                (activated values, Sec. 3.1).  1 <= D <= 64.
- *   H, W         grid sides, H*W = N, 0 <= N <= 2^26.  N == 0 is a no-op.
+ *   H, W         grid sides, H*W = N, 0 <= N <= 2^26 and max(H, W) * D <=
+ *                2^26 (the target passes index columns in 32 bits).  N == 0
+ *                is a no-op.
  *   weights      host, D floats (NULL = all ones): per-channel factors
  *                applied after normalisation (Sec. 3.1, Tab. "params").
  *   carried      device, N x C float32 or NULL: attributes that follow the

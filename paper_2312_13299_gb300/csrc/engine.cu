@@ -518,7 +518,7 @@ int check_job(const plas_job& j, int D, int* skip) {
     *skip = 0;
     if (j.H < 0 || j.W < 0) return fail(PLAS_ERR_INVALID_ARG, "grid sides must be >= 0");
     const long long N = (long long)j.H * j.W;
-    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    if (!grid_fits(j.H, j.W, D)) return fail(PLAS_ERR_INVALID_ARG, "grid %lldx%lld x %d: needs H*W <= 2^26 and max(H, W)*D <= 2^26", (long long)j.H, (long long)j.W, (int)D);
     if (N == 0) {
         *skip = 1;
         return PLAS_OK;
@@ -597,7 +597,7 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
     if (!channels_supported(D))
         return fail(PLAS_ERR_INVALID_ARG, "D=%d not supported (1..16, 20, 24, 32, 48, 64)", D);
     const long long N = (long long)H * W;
-    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    if (!grid_fits(H, W, D)) return fail(PLAS_ERR_INVALID_ARG, "grid %lldx%lld x %d: needs H*W <= 2^26 and max(H, W)*D <= 2^26", (long long)H, (long long)W, (int)D);
     if (C < 0 || (C > 0 && (!carried || !carried_out)))
         return fail(PLAS_ERR_INVALID_ARG, "carried/carried_out required when C > 0");
     plas_schedule s;
@@ -806,7 +806,7 @@ extern "C" int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out
     memset(out, 0, sizeof(*out));
     if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad shape");
     const long long N = (long long)H * W;
-    if (N > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "N=%lld exceeds 2^26", N);
+    if (!grid_fits(H, W, D)) return fail(PLAS_ERR_INVALID_ARG, "grid %lldx%lld x %d: needs H*W <= 2^26 and max(H, W)*D <= 2^26", (long long)H, (long long)W, (int)D);
     cudaStream_t st = (cudaStream_t)stream;
     plas_schedule s;
     plas_default_schedule(&s);

@@ -114,13 +114,20 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
 
     extern __shared__ __align__(16) ulonglong2 ring[];  // kFirRing x 32 lanes x 4 columns
     const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    // column c = (cell, channel): c / D by multiply-high with ceil(2^32 / D),
+    // exact for c < 2^26 and 2 <= D <= 64 (the host keeps max(H, W) * D <=
+    // 2^26); D = 1 is the identity
+    const unsigned dinv = D > 1 ? (unsigned)((0x100000000ull + (unsigned)D - 1) / (unsigned)D) : 0u;
     long long inoff[4];
+    int ccell[4], cch[4];
     bool ok[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int c = c0 + 32 * k + lane;
         ok[k] = c < NC;
-        inoff[k] = ok[k] ? (long long)(c / D) * in_cell + c % D : 0;
+        ccell[k] = D > 1 ? (int)__umulhi((unsigned)c, dinv) : c;
+        cch[k] = c - ccell[k] * D;
+        inoff[k] = ok[k] ? (long long)ccell[k] * in_cell + cch[k] : 0;
     }
 
     // CTA step range: non-zero taps that reach an in-range row for some output
@@ -225,18 +232,16 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
             out = gr.T; out_row = ts; out_cell = (long long)gr.W * ts;
             norm = gr.table + lv.off_nx;
         }
+        const float* rnorm = norm + ((R + 3) & ~3);  // RN(1/n) per position
         long long ooff[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = c0 + 32 * k + lane;
-            ooff[k] = ok[k] ? (long long)(c / D) * out_cell + c % D : 0;
-        }
+        for (int k = 0; k < 4; ++k) ooff[k] = ok[k] ? (long long)ccell[k] * out_cell + cch[k] : 0;
 #pragma unroll
         for (int i = 0; i < X; ++i) {
             const int y = ylo + i;
             if (y < R) {
                 const float nrm = norm[y];
-                const float rcp = __frcp_rn(nrm);  // norms are >= 1 (the centre tap)
+                const float rcp = rnorm[y];
                 float* orow = out + (long long)y * out_row;
                 const float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
 #pragma unroll

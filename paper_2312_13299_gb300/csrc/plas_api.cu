@@ -120,8 +120,9 @@ Geometry build_geometry(const plas_schedule& s, int H, int W) {
         padded_tap_pairs(d.r, H - 1, sigma, &d.ry, &d.rpy, &d.ntpy, ty);
         d.off_tx = (long long)off; off += align_up((size_t)2 * d.ntpx, 4);
         d.off_ty = (long long)off; off += align_up((size_t)2 * d.ntpy, 4);
-        d.off_nx = (long long)off; off += align_up((size_t)W, 4);
-        d.off_ny = (long long)off; off += align_up((size_t)H, 4);
+        // border norms, then their reciprocals, per axis
+        d.off_nx = (long long)off; off += 2 * align_up((size_t)W, 4);
+        d.off_ny = (long long)off; off += 2 * align_up((size_t)H, 4);
         g.table.resize(off, 0.0f);
         std::copy(tx.begin(), tx.end(), g.table.begin() + d.off_tx);
         std::copy(ty.begin(), ty.end(), g.table.begin() + d.off_ty);
@@ -324,7 +325,7 @@ int plas_num_levels(int H, int W, const plas_schedule* sched) {
 }
 
 size_t plas_sort_workspace_bytes(int H, int W, int D) {
-    if (H < 1 || W < 1 || !channels_supported(D) || (long long)H * W > (1LL << 26)) return 0;
+    if (H < 1 || W < 1 || !channels_supported(D) || !grid_fits(H, W, D)) return 0;
     plas_schedule s;
     plas_default_schedule(&s);
     return sort_workspace_bytes(H, W, D, s);
@@ -343,7 +344,7 @@ int plas_target(const float* x, int H, int W, int D, const float* weights, int n
                 const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream) {
     g_last_error.clear();
     if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad sizes");
-    if ((long long)H * W > (1LL << 26)) return fail(PLAS_ERR_INVALID_ARG, "grid too large");
+    if (!grid_fits(H, W, D)) return fail(PLAS_ERR_INVALID_ARG, "grid too large (H*W and max(H, W)*D must be <= 2^26)");
     if (!x || !perm || !T) return fail(PLAS_ERR_INVALID_ARG, "NULL pointer");
     if (!(phi >= 0.0 && phi <= 1e7) || !(sigma_ratio > 0.0)) return fail(PLAS_ERR_INVALID_ARG, "bad phi/sigma");
     cudaStream_t st = (cudaStream_t)stream;

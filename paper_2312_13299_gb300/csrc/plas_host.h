@@ -31,6 +31,11 @@ inline bool channels_supported(int D) {
     return (D >= 1 && D <= 16) || D == 20 || D == 24 || D == 32 || D == 48 || D == 64;
 }
 int validate_schedule(const plas_schedule& s);
+// Grid sizes the kernels index with 32-bit arithmetic: N = H * W <= 2^26 and
+// max(H, W) * D <= 2^26 (a target pass's columns); 0 when they fit.
+inline bool grid_fits(long long H, long long W, int D) {
+    return H * W <= (1LL << 26) && (H > W ? H : W) * D <= (1LL << 26);
+}
 
 // ---- schedule geometry (Sec. 3.1) -----------------------------------------------
 // phi_L = phi0 * shrink^L while >= phi_min; r = floor(phi); beta = min(max(r +

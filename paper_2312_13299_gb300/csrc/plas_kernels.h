@@ -29,7 +29,8 @@ struct Weights {
 
 // Per-level blur geometry.  Taps are stored as duplicated pairs (k, k), padded
 // on the left to a multiple of kFirX ('rp' zero taps before tap -r) and on the
-// right to 'ntp' entries; the border norms follow.
+// right to 'ntp' entries.  The border norms of an axis of length len follow,
+// then (at offset round_up(len, 4)) their reciprocals RN(1/n).
 struct LevelDesc {
     double phi;
     int r;      // floor(phi): blur half-width

@@ -181,6 +181,7 @@ __global__ void norms_kernel(const LevelDesc* __restrict__ lv, int nlev, int H, 
     float n = 0.0f;
     for (int j = jlo; j <= jhi; ++j) n = __fadd_rn(n, taps[2 * (rp + j)]);
     out[pos] = n;
+    out[((len + 3) & ~3) + pos] = __frcp_rn(n);  // RN(1/n), for the correctly rounded division
 }
 
 void launch_norms(const LevelDesc* lv_dev, int nlev, int H, int W, float* table,

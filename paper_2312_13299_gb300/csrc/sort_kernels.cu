@@ -62,8 +62,11 @@ __device__ __forceinline__ float sqdist(const float* g, const float* t) {
     return acc;
 }
 
-__device__ __forceinline__ unsigned long long fixed_point(float e, double scale) {
-    return (unsigned long long)__double2ll_rn(__dmul_rn((double)e, scale));
+// rint(e * 2^k) as an integer.  Scaling by a power of two is exact in FP32
+// (e * 2^k < 2^62 here), so this equals rint((double)e * 2^k) without the
+// FP64 pipe.
+__device__ __forceinline__ unsigned long long fixed_point(float e, float scale) {
+    return (unsigned long long)__float2ll_rn(__fmul_rn(e, scale));
 }
 
 // The 24 permutations of four positions in lexicographic order, generated at
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     const int ngroups = (beta * beta) / 4;
     // N <= 2^26 (checked on the host), so every cell and group index fits 32 bits
     const int ngt = nby * nbx * ngroups;
-    const double scale = ldexp(1.0, st->scale_exp);
+    const float scale = ldexpf(1.0f, st->scale_exp);  // 2^k, 0 <= k <= 32
     float* __restrict__ G = gr.G;
     const float* __restrict__ T = gr.T;
     const uint32_t* __restrict__ pi = gr.pi;
@@ -210,28 +213,34 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) C[i][j] = __shfl_sync(0xFFFFFFFFu, c[j], qbase | i);
-        float best = 0.0f;
-        int bidx = 0;
+        // first strict minimum in lexicographic order, as a pairwise tree:
+        // the left operand always holds the earlier permutations and wins
+        // ties, so the tree picks the same permutation as a sequential scan.
+        // Each node carries its permutation packed as four 2-bit targets.
+        float bc[24];
+        int bp[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) {
-            const float cost = __fadd_rn(
-                __fadd_rn(__fadd_rn(C[0][kPerm24.p[k][0]], C[1][kPerm24.p[k][1]]),
-                          C[2][kPerm24.p[k][2]]),
-                C[3][kPerm24.p[k][3]]);
-            if (k == 0 || cost < best) {
-                best = cost;
-                bidx = k;
+            bc[k] = __fadd_rn(__fadd_rn(__fadd_rn(C[0][kPerm24.p[k][0]], C[1][kPerm24.p[k][1]]),
+                                        C[2][kPerm24.p[k][2]]),
+                              C[3][kPerm24.p[k][3]]);
+            bp[k] = kPerm24.p[k][0] | (kPerm24.p[k][1] << 2) | (kPerm24.p[k][2] << 4) |
+                    (kPerm24.p[k][3] << 6);
+        }
+#pragma unroll
+        for (int n = 24; n > 1; n = (n + 1) / 2) {
+#pragma unroll
+            for (int m = 0; m < n / 2; ++m) {
+                const bool right = bc[2 * m + 1] < bc[2 * m];
+                bc[m] = right ? bc[2 * m + 1] : bc[2 * m];
+                bp[m] = right ? bp[2 * m + 1] : bp[2 * m];
+            }
+            if (n & 1) {
+                bc[n / 2] = bc[n - 1];
+                bp[n / 2] = bp[n - 1];
             }
         }
-        int sg[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int v = 0;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) v = (bidx == k) ? kPerm24.p[k][i] : v;
-            sg[i] = v;
-        }
-        const int my_dst = pick4i(sg, qi);
+        const int my_dst = (bp[0] >> (2 * qi)) & 3;
         if (active) {
             float4* dst = reinterpret_cast<float4*>(G + (size_t)pick4i(pos, my_dst) * GS);
 #pragma unroll
