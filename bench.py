@@ -284,9 +284,17 @@ def run_plas(args):
     ws = torch.empty(plas.sort_workspace_bytes(side, side, D), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # launch shapes for this grid shape (the results do not depend on them)
+    # launch shapes for this grid shape (the results do not depend on them):
+    # measured by the autotuner, or pinned with --tune SMALL_BELOW,CTAS_PER_SM
+    # (a profiler distorts the tuner's own timings, so profiled runs pin the
+    # values a plain run chose)
     t_tune = time.perf_counter()
-    tune = plas.autotune(side, side, D)
+    if args.tune == "auto":
+        tune = plas.autotune(side, side, D)
+    else:
+        sb, per = (int(v) for v in args.tune.split(","))
+        plas.set_tuning(side, side, D, fir_small_below=sb, assign_ctas_per_sm=per)
+        tune = plas.get_tuning(side, side, D)
     t_tune = time.perf_counter() - t_tune
 
     def step(profile):
@@ -369,6 +377,7 @@ def run_plas(args):
                    "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush",
                    "tuning": {"fir_small_below": tune["fir_small_below"],
                               "assign_ctas_per_sm": tune["assign_ctas_per_sm"],
+                              "source": "autotune" if args.tune == "auto" else "pinned",
                               "autotune_s": round(t_tune, 2)}},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -599,6 +608,8 @@ def main():
     ap.add_argument("--impl", default="plas", choices=["plas", "reference"])
     ap.add_argument("--workload", default="m1", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--tune", default="auto", help="'auto' (run the autotuner) or "
+                    "SMALL_BELOW,CTAS_PER_SM to pin the launch shapes")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="run one sort of the workload capped at ITERS iterations and exit "
                          "(a small, bounded program for ncu captures; prints nothing)")

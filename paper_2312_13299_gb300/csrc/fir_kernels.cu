@@ -39,7 +39,11 @@ struct FirTiling {
     static constexpr int TY = TY_, RING = RING_, CH = CH_, MINB = MINB_;
     static constexpr int THREADS = 32 * TY / kFirX;
     static_assert(RING >= 2 * CH + TY + kFirX, "ring must hold two chunks + span");
-    static_assert((RING & (RING - 1)) == 0 && CH % kFirX == 0, "ring power of two, chunk of 8s");
+    static_assert(RING % kFirX == 0 && CH % kFirX == 0, "ring and chunk in whole steps of 8");
+    // ring slot of input row t (t >= 0)
+    __device__ static __forceinline__ int slot(int t) {
+        return (RING & (RING - 1)) == 0 ? (t & (RING - 1)) : (t % RING);
+    }
 };
 using FirLarge = FirTiling<128, 256, 56, 1>;
 using FirSmall = FirTiling<32, 64, 8, 4>;
@@ -64,10 +68,11 @@ __device__ __forceinline__ float div_rn(float a, float b, float y) {
     return __fmaf_rn(r, y, q);
 }
 
-__device__ __forceinline__ void cp_async_f32(float* sdst, const float* gsrc, bool valid) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    const int n = valid ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n)
+// 4-byte copy to shared address sa + OFF (n = 4: copy, n = 0: zero-fill)
+template <int OFF>
+__device__ __forceinline__ void cp_async_f32_at(unsigned sa, const float* gsrc, int n) {
+    asm volatile("cp.async.ca.shared.global [%0+%3], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n),
+                 "n"(OFF)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
@@ -83,9 +88,8 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
     int pass, const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, int D, int gs,
     int ts) {
     constexpr int X = kFirX;
-    constexpr int kFirTY = TL::TY, kFirRing = TL::RING, kFirChunk = TL::CH;
+    constexpr int kFirTY = TL::TY, kFirChunk = TL::CH;
     constexpr int kFirThreads = TL::THREADS;
-    constexpr int RM = kFirRing - 1;
     constexpr int NW = kFirThreads / 32;
     const CtaRef cr = resolve_cta(map);
     const GridRef& gr = grids[cr.g];
@@ -146,13 +150,32 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
     const int wend = min(jend, (whi + X) / X * X);
 
     const int span = kFirTY + X;  // rows read past the last step of a chunk
-    auto fetch = [&](int t) {
-        const int yy = t0 - rp + t;
-        const bool rowok = yy >= 0 && yy < R;
-        float* dst = reinterpret_cast<float*>(ring + (t & RM) * 32 + lane);
-        const float* base = in + (rowok ? (long long)yy * in_row : 0);
+    // row fetch: ring row t holds input row t0 - rp + t (zero outside [0, R));
+    // per lane the four column pointers, copy sizes and the ring address are
+    // set up once, so a row costs one multiply, four 64-bit adds and four copies
+    const float* colp[4];
+    int csz[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) cp_async_f32(dst + k, base + inoff[k], rowok && ok[k]);
+    for (int k = 0; k < 4; ++k) {
+        colp[k] = in + inoff[k];
+        csz[k] = ok[k] ? 4 : 0;
+    }
+    const int tlo = rp - t0, thi = rp - t0 + R;  // ring rows holding grid rows
+    const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring) + 16u * (unsigned)lane;
+    auto fetch = [&](int t) {
+        const unsigned sa = ring_sa + 512u * (unsigned)TL::slot(t);
+        if (t >= tlo && t < thi) {  // warp-uniform
+            const long long off = (long long)(t - tlo) * in_row;
+            cp_async_f32_at<0>(sa, colp[0] + off, csz[0]);
+            cp_async_f32_at<4>(sa, colp[1] + off, csz[1]);
+            cp_async_f32_at<8>(sa, colp[2] + off, csz[2]);
+            cp_async_f32_at<12>(sa, colp[3] + off, csz[3]);
+        } else {
+            cp_async_f32_at<0>(sa, colp[0], 0);
+            cp_async_f32_at<4>(sa, colp[1], 0);
+            cp_async_f32_at<8>(sa, colp[2], 0);
+            cp_async_f32_at<12>(sa, colp[3], 0);
+        }
     };
     // taps of a chunk, (k, k) pairs, double-buffered next to the ring
     __shared__ __align__(16) unsigned long long tapbuf[2][kFirChunk];
@@ -189,11 +212,11 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
             if (s0 < s1) {
                 if (!started) {
 #pragma unroll
-                    for (int u = 0; u < X; ++u) win[u] = fring[((rbase + s0 + u) & RM) * 32 + lane];
+                    for (int u = 0; u < X; ++u) win[u] = fring[TL::slot(rbase + s0 + u) * 32 + lane];
                     started = true;
                 }
                 for (int jb = s0; jb < s1; jb += X) {
-                    const int nb = (rbase + jb + X) & RM;
+                    const int nb = TL::slot(rbase + jb + X);  // a multiple of 8: nb + 7 < RING
 #pragma unroll
                     for (int u = 0; u < X; u += 2) {
                         // taps of steps jb+u and jb+u+1 as two (k, k) pairs
