@@ -116,6 +116,8 @@ def lib():
             L.orc_smooth_taps64.argtypes = [d, i, P(d)]
             L.orc_smooth_loss64.argtypes = [P(d), i, i, i, d, i, P(d), d, P(d)]
             L.orc_smooth_loss64.restype = d
+            L.orc_smooth_loss64_huber.argtypes = [P(d), i, i, i, d, i, P(d), d, d, P(d)]
+            L.orc_smooth_loss64_huber.restype = d
             L.orc_num_threads.restype = i
             _lib = L
     return _lib
@@ -290,14 +292,20 @@ def smooth_taps64(sigma: float, ksize: int) -> np.ndarray:
 
 
 def smooth_loss64(x: np.ndarray, sigma: float = 1.0, ksize: int = 7, lam=None,
-                  grad_loss: float = 1.0, want_grad: bool = True):
-    """x: H x W x C (any float dtype, used in FP64) -> (loss, grad or None)."""
+                  grad_loss: float = 1.0, want_grad: bool = True, huber_delta: float = 0.0):
+    """x: H x W x C (any float dtype, used in FP64) -> (loss, grad or None).
+    huber_delta > 0 selects the Huber form of Sec. 3.2, else the squared form."""
     x = np.ascontiguousarray(x, np.float64)
     H, W, C = x.shape
     lam = None if lam is None else np.ascontiguousarray(lam, np.float64)
     g = np.zeros_like(x) if want_grad else None
-    L = lib().orc_smooth_loss64(_p(x, ctypes.c_double), H, W, C, sigma, ksize,
-                                _p(lam, ctypes.c_double), grad_loss, _p(g, ctypes.c_double))
+    if huber_delta > 0:
+        L = lib().orc_smooth_loss64_huber(_p(x, ctypes.c_double), H, W, C, sigma, ksize,
+                                          _p(lam, ctypes.c_double), huber_delta, grad_loss,
+                                          _p(g, ctypes.c_double))
+    else:
+        L = lib().orc_smooth_loss64(_p(x, ctypes.c_double), H, W, C, sigma, ksize,
+                                    _p(lam, ctypes.c_double), grad_loss, _p(g, ctypes.c_double))
     return L, g
 
 

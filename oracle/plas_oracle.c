@@ -687,6 +687,45 @@ double orc_smooth_loss64(const double* x, int H, int W, int C, double sigma, int
     return L;
 }
 
+/* Huber form of the smoothness loss (Sec. 3.2: the deviation of each cell
+ * from the blurred grid is penalised with a Huber loss, less sensitive to
+ * outliers than the squared error):
+ *   h(r) = r^2 / 2 for |r| <= delta, delta * (|r| - delta / 2) otherwise,
+ *   L = (1/M) sum lam_c h(x - Bx),
+ *   dL/dx = (g/M) (psi - B psi),  psi = lam_c * clamp(x - Bx, -delta, delta)
+ * (B symmetric with zero padding, so B^T = B).  delta > 0. */
+double orc_smooth_loss64_huber(const double* x, int H, int W, int C, double sigma, int ksize,
+                               const double* lam, double delta, double grad_loss,
+                               double* grad /* or NULL */)
+{
+    const long M = (long)H * W * C;
+    const int h = ksize / 2;
+    double* b = (double*)malloc(sizeof(double) * (size_t)(2 * h + 1));
+    double* bx = (double*)malloc(sizeof(double) * (size_t)M);
+    double* psi = (double*)malloc(sizeof(double) * (size_t)M);
+    orc_smooth_taps64(sigma, ksize, b);
+    orc_blur64(x, H, W, C, b, h, bx);
+    double L = 0.0;
+    for (long i = 0; i < M; ++i) {
+        const double l = lam ? lam[i % C] : 1.0;
+        const double r = x[i] - bx[i];
+        const double a = fabs(r);
+        L += l * (a <= delta ? 0.5 * r * r : delta * (a - 0.5 * delta));
+        psi[i] = l * (r < -delta ? -delta : (r > delta ? delta : r));
+    }
+    L /= (double)M;
+    if (grad) {
+        double* bpsi = (double*)malloc(sizeof(double) * (size_t)M);
+        orc_blur64(psi, H, W, C, b, h, bpsi);
+        for (long i = 0; i < M; ++i) grad[i] = grad_loss / (double)M * (psi[i] - bpsi[i]);
+        free(bpsi);
+    }
+    free(psi);
+    free(bx);
+    free(b);
+    return L;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
