@@ -558,9 +558,17 @@ def run_loss(args):
     C = x.shape[2]
     g = torch.ones((), device="cuda")
     peaks, psrc = _peaks()
+    lam_paper = torch.from_numpy(synth.paper_smoothness_weights()).cuda()
     out = {}
+    # the benchmark configuration (squared form, sigma 1, 7x7, unit weights)
+    # and the paper's regulariser (Huber delta 1, kernel 5, sigma 3, weights
+    # 0.09 opacity / 0.91 rotation)
     for name, fn, bpe in [("fwd", lambda: plas.smooth_loss_fwd(x), 4),
-                          ("bwd", lambda: plas.smooth_loss_bwd(x, g), 8)]:
+                          ("bwd", lambda: plas.smooth_loss_bwd(x, g), 8),
+                          ("huber_paper_fwd", lambda: plas.smooth_loss_fwd(
+                              x, 3.0, 5, lam_paper, huber_delta=1.0), 4),
+                          ("huber_paper_bwd", lambda: plas.smooth_loss_bwd(
+                              x, g, 3.0, 5, lam_paper, huber_delta=1.0), 8)]:
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()

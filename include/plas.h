@@ -275,6 +275,25 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
                          void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * The same pair with the penalty chosen by huber_delta (host float, finite,
+ * >= 0).  0: the squared form above.  delta > 0: the Huber form that Sec.
+ * 3.2 names for the deviation from the blurred grid (delta is not stated in
+ * the paper; PyTorch's default is 1.0):
+ *   h(r) = r^2 / 2 for |r| <= delta, delta * (|r| - delta / 2) otherwise,
+ *   loss = (1/M) * sum lam_c * h(r),
+ *   dloss/dx = (g / M) * (psi - B psi),  psi = lam_c * clamp(r, -delta, delta).
+ * The paper's configuration (supplementary, Tab. "params") is ksize 5,
+ * sigma 3, weights 0.09 on opacity and 0.91 on the rotation channels.
+ * Arguments, layout, workspace and errors as above.
+ */
+int plas_smooth_loss_fwd_ex(const float* x, int H, int W, int C, float sigma, int ksize,
+                            const float* ch_weights, float huber_delta, float* loss,
+                            void* workspace, size_t ws_bytes, void* stream);
+int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, int ksize,
+                            const float* ch_weights, float huber_delta, const float* grad_loss,
+                            float* grad_x, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * plas_smooth_loss_fwd_noalloc -- the same loss as plas_smooth_loss_fwd, for
  * callers that cannot allocate device memory during the call: a host loop
  * whose memory is owned by another allocator with a fixed budget, or a
@@ -295,6 +314,31 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
  */
 int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigma, int ksize,
                                  const float* ch_weights, float* loss, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* quantisation of the sorted attribute grids (Sec. 3.3)                   */
+/* ---------------------------------------------------------------------- */
+/*
+ * After training, each attribute channel of the sorted grid is clipped to a
+ * range and rounded to the nearest of q equally spaced values (Sec. 3.3,
+ * "Quantization & Compression"; the paper's q: 2^14 for coordinates, 2^6
+ * for scale, opacity and rotation, 2^5 for the SH rest; its clip ranges:
+ * DC colour [-2, 4], opacity [-6, 12], SH rest [-1, 1], rotation [-1, 2]).
+ *   code = rint(t * (q - 1)),  t = (min(max(x, lo), hi) - lo) / (hi - lo)
+ * in FP32 with IEEE division and round-half-to-even (hi == lo gives 0; NaN
+ * gives 0).  plas_dequantize maps codes back:
+ *   x' = lo + code * ((hi - lo) / (q - 1)).
+ * x / out: device N x C float32 (row-major, channel fastest); codes: device
+ * N x C uint16; lo, hi: host C floats (finite, lo <= hi); q: host C ints in
+ * [2, 65536]; 1 <= C <= 256.  Enqueued on 'stream'.  Errors:
+ * PLAS_ERR_INVALID_ARG, PLAS_ERR_CUDA.  The paper has no kernel for this
+ * step; the codec that stores the planes (JPEG XL) is not part of this
+ * library.
+ */
+int plas_quantize(const float* x, long long N, int C, const float* lo, const float* hi,
+                  const int* q, uint16_t* codes, void* stream);
+int plas_dequantize(const uint16_t* codes, long long N, int C, const float* lo,
+                    const float* hi, const int* q, float* out, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* batched sort: many independent grids advanced together                 */

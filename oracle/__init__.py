@@ -118,6 +118,8 @@ def lib():
             L.orc_smooth_loss64.restype = d
             L.orc_smooth_loss64_huber.argtypes = [P(d), i, i, i, d, i, P(d), d, d, P(d)]
             L.orc_smooth_loss64_huber.restype = d
+            L.orc_quantize.argtypes = [f, ctypes.c_long, i, f, f, P(i),
+                                       P(ctypes.c_ushort)]
             L.orc_num_threads.restype = i
             _lib = L
     return _lib
@@ -307,6 +309,20 @@ def smooth_loss64(x: np.ndarray, sigma: float = 1.0, ksize: int = 7, lam=None,
         L = lib().orc_smooth_loss64(_p(x, ctypes.c_double), H, W, C, sigma, ksize,
                                     _p(lam, ctypes.c_double), grad_loss, _p(g, ctypes.c_double))
     return L, g
+
+
+def quantize(x: np.ndarray, lo, hi, q) -> np.ndarray:
+    """Sec. 3.3 quantisation codes (uint16) of an [N, C] float32 array."""
+    x = _f32(x)
+    C = x.shape[-1]
+    n = x.size // C
+    lo_a, hi_a = _f32(lo), _f32(hi)
+    q_a = np.ascontiguousarray(q, np.int32)
+    out = np.zeros(x.shape, np.uint16)
+    lib().orc_quantize(_p(x, ctypes.c_float), n, C, _p(lo_a, ctypes.c_float),
+                       _p(hi_a, ctypes.c_float), _p(q_a, ctypes.c_int),
+                       _p(out, ctypes.c_ushort))
+    return out
 
 
 def num_threads() -> int:

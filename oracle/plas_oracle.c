@@ -726,6 +726,25 @@ double orc_smooth_loss64_huber(const double* x, int H, int W, int C, double sigm
     return L;
 }
 
+/* Quantisation of Sec. 3.3: clip channel c to [lo_c, hi_c], map linearly to
+ * [0, 1] and round to the nearest of q_c equally spaced values (FP32, the
+ * integer decided by rounding half to even; hi == lo gives 0).  Written
+ * out as the definition; fmaxf/fminf send NaN to the bound. */
+void orc_quantize(const float* x, long n, int C, const float* lo, const float* hi, const int* q,
+                  unsigned short* codes)
+{
+    for (long i = 0; i < n * C; ++i) {
+        const int c = (int)(i % C);
+        int k = 0;
+        if (hi[c] > lo[c]) {
+            const float v = fminf(fmaxf(x[i], lo[c]), hi[c]);
+            const float t = (v - lo[c]) / (hi[c] - lo[c]);
+            k = (int)rintf(t * (float)(q[c] - 1));
+        }
+        codes[i] = (unsigned short)k;
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

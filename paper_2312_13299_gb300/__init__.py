@@ -430,27 +430,67 @@ def grid_metrics(grid: torch.Tensor, scale: float = 1.0):
     return out[0], out[1], out[2]
 
 
+def _quant_args(C, lo, hi, q):
+    lo_a = (ctypes.c_float * C)(*[float(v) for v in lo])
+    hi_a = (ctypes.c_float * C)(*[float(v) for v in hi])
+    q_a = (ctypes.c_int * C)(*[int(v) for v in q])
+    return lo_a, hi_a, q_a
+
+
+def quantize(x: torch.Tensor, lo, hi, q) -> torch.Tensor:
+    """Sec. 3.3 quantisation of an [N, C] (or [..., C]) float32 grid: clip
+    channel c to [lo[c], hi[c]] and round to the nearest of q[c] levels.
+    Returns the codes as int16 storage holding uint16 values (view with
+    .to(torch.int32) & 0xFFFF to read them)."""
+    x = _need_cuda(x, "x")
+    C = x.shape[-1]
+    N = x.numel() // C
+    codes = torch.empty(x.shape, dtype=torch.int16, device=x.device)
+    lo_a, hi_a, q_a = _quant_args(C, lo, hi, q)
+    with torch.cuda.device(x.device):
+        rc = load().plas_quantize(x.data_ptr(), N, C, lo_a, hi_a, q_a, codes.data_ptr(),
+                                  _stream(x.device))
+    check(rc, "plas_quantize")
+    return codes
+
+
+def dequantize(codes: torch.Tensor, lo, hi, q) -> torch.Tensor:
+    codes = _need_cuda(codes, "codes", torch.int16)
+    C = codes.shape[-1]
+    N = codes.numel() // C
+    out = torch.empty(codes.shape, dtype=torch.float32, device=codes.device)
+    lo_a, hi_a, q_a = _quant_args(C, lo, hi, q)
+    with torch.cuda.device(codes.device):
+        rc = load().plas_dequantize(codes.data_ptr(), N, C, lo_a, hi_a, q_a, out.data_ptr(),
+                                    _stream(codes.device))
+    check(rc, "plas_dequantize")
+    return out
+
+
 def _lam_ptr(lam: Optional[torch.Tensor]):
     return lam.data_ptr() if lam is not None else None
 
 
 def smooth_loss_fwd(x: torch.Tensor, sigma: float = 1.0, ksize: int = 7,
-                    lam: Optional[torch.Tensor] = None) -> torch.Tensor:
+                    lam: Optional[torch.Tensor] = None, huber_delta: float = 0.0) -> torch.Tensor:
+    """Sec. 3.2 smoothness loss of an [H, W, C] grid (squared form, or the
+    Huber form when huber_delta > 0)."""
     x = _need_cuda(x, "x")
     H, W, C = x.shape
     if lam is not None:
         lam = _need_cuda(lam, "lam")
     loss = torch.empty((), dtype=torch.float32, device=x.device)
     with torch.cuda.device(x.device):
-        rc = load().plas_smooth_loss_fwd(x.data_ptr(), H, W, C, float(sigma), int(ksize),
-                                         _lam_ptr(lam), loss.data_ptr(), None, 0,
-                                         _stream(x.device))
-    check(rc, "plas_smooth_loss_fwd")
+        rc = load().plas_smooth_loss_fwd_ex(x.data_ptr(), H, W, C, float(sigma), int(ksize),
+                                            _lam_ptr(lam), float(huber_delta), loss.data_ptr(),
+                                            None, 0, _stream(x.device))
+    check(rc, "plas_smooth_loss_fwd_ex")
     return loss
 
 
 def smooth_loss_bwd(x: torch.Tensor, grad_loss: torch.Tensor, sigma: float = 1.0,
-                    ksize: int = 7, lam: Optional[torch.Tensor] = None) -> torch.Tensor:
+                    ksize: int = 7, lam: Optional[torch.Tensor] = None,
+                    huber_delta: float = 0.0) -> torch.Tensor:
     x = _need_cuda(x, "x")
     H, W, C = x.shape
     if lam is not None:
@@ -458,23 +498,24 @@ def smooth_loss_bwd(x: torch.Tensor, grad_loss: torch.Tensor, sigma: float = 1.0
     g = _need_cuda(grad_loss.reshape(()).to(torch.float32), "grad_loss")
     grad = torch.empty_like(x)
     with torch.cuda.device(x.device):
-        rc = load().plas_smooth_loss_bwd(x.data_ptr(), H, W, C, float(sigma), int(ksize),
-                                         _lam_ptr(lam), g.data_ptr(), grad.data_ptr(), None, 0,
-                                         _stream(x.device))
-    check(rc, "plas_smooth_loss_bwd")
+        rc = load().plas_smooth_loss_bwd_ex(x.data_ptr(), H, W, C, float(sigma), int(ksize),
+                                            _lam_ptr(lam), float(huber_delta), g.data_ptr(),
+                                            grad.data_ptr(), None, 0, _stream(x.device))
+    check(rc, "plas_smooth_loss_bwd_ex")
     return grad
 
 
 class SmoothLoss(torch.autograd.Function):
-    """Sec. 3.2 smoothness loss L = mean(lam_c (x - Bx)^2) with a hand-written
+    """Sec. 3.2 smoothness loss L = mean(lam_c h(x - Bx)), h the squared
+    deviation or (huber_delta > 0) the Huber penalty, with a hand-written
     backward kernel.  x: [H, W, C] float32 CUDA, channel-last."""
 
     @staticmethod
-    def forward(ctx, x, sigma=1.0, ksize=7, lam=None):
-        ctx.sigma, ctx.ksize = sigma, ksize
+    def forward(ctx, x, sigma=1.0, ksize=7, lam=None, huber_delta=0.0):
+        ctx.sigma, ctx.ksize, ctx.huber_delta = sigma, ksize, huber_delta
         ctx.save_for_backward(x, lam) if lam is not None else ctx.save_for_backward(x)
         ctx.has_lam = lam is not None
-        return smooth_loss_fwd(x, sigma, ksize, lam)
+        return smooth_loss_fwd(x, sigma, ksize, lam, huber_delta)
 
     @staticmethod
     def backward(ctx, g):
@@ -482,9 +523,10 @@ class SmoothLoss(torch.autograd.Function):
             x, lam = ctx.saved_tensors
         else:
             (x,), lam = ctx.saved_tensors, None
-        return smooth_loss_bwd(x, g, ctx.sigma, ctx.ksize, lam), None, None, None
+        return (smooth_loss_bwd(x, g, ctx.sigma, ctx.ksize, lam, ctx.huber_delta),
+                None, None, None, None)
 
 
 def smooth_loss(x: torch.Tensor, sigma: float = 1.0, ksize: int = 7,
-                lam: Optional[torch.Tensor] = None) -> torch.Tensor:
-    return SmoothLoss.apply(x, sigma, ksize, lam)
+                lam: Optional[torch.Tensor] = None, huber_delta: float = 0.0) -> torch.Tensor:
+    return SmoothLoss.apply(x, sigma, ksize, lam, huber_delta)

@@ -98,8 +98,16 @@ SIGNATURES = {
                                      c_void_p, c_void_p, c_size_t, c_void_p]),
     "plas_smooth_loss_bwd": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "plas_smooth_loss_fwd_ex": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int, c_void_p,
+                                        c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "plas_smooth_loss_bwd_ex": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int, c_void_p,
+                                        c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "plas_smooth_loss_fwd_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int,
                                              c_void_p, c_void_p, c_void_p]),
+    "plas_quantize": (c_int, [c_void_p, c_ll, c_int, P(c_float), P(c_float), P(c_int), c_void_p,
+                              c_void_p]),
+    "plas_dequantize": (c_int, [c_void_p, c_ll, c_int, P(c_float), P(c_float), P(c_int),
+                                c_void_p, c_void_p]),
     "plas_batch_workspace_bytes": (c_size_t, [c_int, P(plas_job), c_int]),
     "plas_batch_sort": (c_int, [c_int, P(plas_job), c_int, P(c_float), P(plas_schedule),
                                 c_void_p, c_size_t, c_void_p]),

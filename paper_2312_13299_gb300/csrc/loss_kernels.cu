@@ -46,12 +46,30 @@ struct Taps {
     float b[2 * kMaxH + 1];
 };
 
+// The penalty of a residual v and the value the backward's first pass
+// stores: squared form (hd <= 0): v^2 and v; Huber form (hd = delta > 0):
+// v^2 / 2 or delta (|v| - delta / 2), and clamp(v, -delta, delta).
+__device__ __forceinline__ float loss_term(float v, float hd) {
+    if (hd > 0.0f) {
+        const float a = fabsf(v);
+        return a <= hd ? __fmul_rn(0.5f, __fmul_rn(v, v)) : __fmul_rn(hd, __fsub_rn(a, 0.5f * hd));
+    }
+    return __fmul_rn(v, v);
+}
+__device__ __forceinline__ float resid_out(float v, float hd) {
+    return hd > 0.0f ? fminf(fmaxf(v, -hd), hd) : v;
+}
+// gradient scale: 2 g / M for the squared form, g / M for Huber
+__device__ __forceinline__ float grad_coef(const float* gscalar, double inv_m, float hd) {
+    return (float)((hd > 0.0f ? 1.0 : 2.0) * (double)(*gscalar) * inv_m);
+}
+
 
 template <bool GRAD>
 __global__ void __launch_bounds__(kThreads) smooth_kernel(
     const float* __restrict__ u, int H, int W, int C, int h, Taps tp,
     const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
-    double inv_m, double* __restrict__ partials) {
+    double inv_m, float hd, double* __restrict__ partials) {
     extern __shared__ __align__(16) float sm[];
     const int x0 = blockIdx.x * kTX;
     const int y0 = blockIdx.y * kTYS;
@@ -64,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(
     const int tid = threadIdx.x;
     double part = 0.0;
     float coef = 0.0f;
-    if (GRAD) coef = (float)(2.0 * (double)(*gscalar) * inv_m);
+    if (GRAD) coef = grad_coef(gscalar, inv_m, hd);
 
     const int ylast = min(y0 + kTYS, H) - 1;
     for (int yi = y0 - h; yi <= ylast + h; ++yi) {
@@ -103,8 +121,8 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(
                 if (GRAD) {
                     out[cbase + e] = __fmul_rn(__fmul_rn(coef, l), v);
                 } else {
-                    if (out) out[cbase + e] = v;
-                    part += (double)l * (double)v * (double)v;
+                    if (out) out[cbase + e] = resid_out(v, hd);
+                    part += (double)l * (double)loss_term(v, hd);
                 }
             }
         }
@@ -125,104 +143,7 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(
     }
 }
 
-constexpr int kXB = 4;           // cells per thread (stream_kernel)
-constexpr int kStreamThreads = 128;
-constexpr int kStreamMaxH = 7;
-
-template <int HH, bool GRAD>
-__global__ void __launch_bounds__(kStreamThreads, 8) stream_kernel(
-    const float* __restrict__ u, int H, int W, int C, int band, Taps tp,
-    const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
-    double inv_m, double* __restrict__ partials) {
-    constexpr int R = 2 * HH + 1;
-    constexpr int NV = kXB + 2 * HH;
-    const int nxb = (W + kXB - 1) / kXB;
-    const long long gid = (long long)blockIdx.x * kStreamThreads + threadIdx.x;
-    const bool live = gid < (long long)nxb * C;
-    const int c = live ? (int)(gid % C) : 0;
-    const int x0 = live ? (int)(gid / C) * kXB : 0;
-    const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);  // output rows [y0, y1)
-    const float* b = tp.b;  // kernel parameter (constant bank)
-    const float l = (lam && live) ? __ldg(lam + c) : 1.0f;
-    float coef = 0.0f;
-    if (GRAD) coef = __fmul_rn((float)(2.0 * (double)(*gscalar) * inv_m), l);
-    const long long rowstride = (long long)W * C;
-    const float* __restrict__ uc = u + c + (long long)(x0 - HH) * C;  // cell x0 - HH of row 0
-    // the loads of one input row (zero outside the grid)
-    auto load_row = [&](int yi, float* v) {
-        const bool yok = live && yi >= 0 && yi < H;
-        const float* row = uc + (long long)yi * rowstride;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const int xs = x0 - HH + k;
-            v[k] = (yok && (unsigned)xs < (unsigned)W) ? __ldg(row + k * C) : 0.0f;
-        }
-    };
-
-    float hr[R][kXB];  // x-blurred rows; row yi sits in slot (yi - ystart) mod R
-    double part = 0.0;
-    float band_acc = 0.0f;
-    const int ystart = y0 - HH, yend = y1 + HH;  // input rows [ystart, yend)
-    float vn[NV];  // the next row's values, loaded one row ahead
-    load_row(ystart, vn);
-    for (int yb = ystart; yb < yend; yb += R) {
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int yi = yb + q;
-            if (yi < yend) {  // uniform over the CTA
-                float v[NV];
-#pragma unroll
-                for (int k = 0; k < NV; ++k) v[k] = vn[k];
-                if (yi + 1 < yend) load_row(yi + 1, vn);
-#pragma unroll
-                for (int i = 0; i < kXB; ++i) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < R; ++j) acc = __fmaf_rn(b[j], v[i + j], acc);
-                    hr[q][i] = acc;
-                }
-                const int yc = yi - HH;  // the output row whose ring is now full
-                if (yc >= y0) {
-                    const float* crow = uc + (long long)yc * rowstride + HH * C;
-                    float sq = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < kXB; ++i) {
-                        float acc = 0.0f;
-#pragma unroll
-                        for (int j = 0; j < R; ++j) acc = __fmaf_rn(b[j], hr[(q + 1 + j) % R][i], acc);
-                        const int xc = x0 + i;
-                        if (live && xc < W) {
-                            const float vv = __fsub_rn(__ldg(crow + i * C), acc);
-                            const long long o = (long long)yc * rowstride + (long long)xc * C + c;
-                            if (GRAD) {
-                                out[o] = __fmul_rn(coef, vv);
-                            } else {
-                                if (out) out[o] = vv;
-                                sq = __fmaf_rn(vv, vv, sq);
-                            }
-                        }
-                    }
-                    if (!GRAD) band_acc = __fmaf_rn(l, sq, band_acc);
-                }
-            }
-        }
-        if (!GRAD) {  // at most R rows x kXB cells in one FP32 partial
-            part += (double)band_acc;
-            band_acc = 0.0f;
-        }
-    }
-    if (!GRAD) {
-        __shared__ double red[kStreamThreads / 32];
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, off);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s2 = 0.0;
-            for (int w = 0; w < kStreamThreads / 32; ++w) s2 += red[w];
-            partials[blockIdx.y * gridDim.x + blockIdx.x] = s2;
-        }
-    }
-}
+constexpr int kStreamMaxH = 7;  // largest half-width of the staged kernel
 
 // ---------------------------------------------------------------------------
 // staged_kernel (h <= 7, C <= 256): each input row of the CTA's span (cells
@@ -258,11 +179,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // iteration (the blurred row and the centre row h rows above it)
 __host__ __device__ constexpr int sg_slots(int h) { return kSgAhead + h + 2; }
 
-template <int HH, bool GRAD>
+template <int HH, bool GRAD, bool HUBER>
 __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, int W, int C,
                                             int band, int G, int slot_f, const Taps& tp,
                                             const float* __restrict__ lam, float* __restrict__ out,
-                                            float coef0, double* __restrict__ partials,
+                                            float coef0, float hd, double* __restrict__ partials,
                                             float* __restrict__ sg) {
     constexpr int R = 2 * HH + 1;
     constexpr int NS = sg_slots(HH);
@@ -371,11 +292,14 @@ __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, 
                                 if (xb < W) out[o + NP * C] = gv.y;
                             } else {
                                 if (out) {
-                                    if (xa < W) out[o] = vv.x;
-                                    if (xb < W) out[o + NP * C] = vv.y;
+                                    if (xa < W) out[o] = HUBER ? resid_out(vv.x, hd) : vv.x;
+                                    if (xb < W) out[o + NP * C] = HUBER ? resid_out(vv.y, hd) : vv.y;
                                 }
                                 const float2 m2 = make_float2(xa < W ? vv.x : 0.0f, xb < W ? vv.y : 0.0f);
-                                sq = __ffma2_rn(m2, m2, sq);
+                                if (HUBER)
+                                    sq = __fadd2_rn(sq, make_float2(loss_term(m2.x, hd), loss_term(m2.y, hd)));
+                                else
+                                    sq = __ffma2_rn(m2, m2, sq);
                             }
                         }
                     }
@@ -407,14 +331,14 @@ __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, 
     }
 }
 
-template <int HH, bool GRAD>
+template <int HH, bool GRAD, bool HUBER>
 __global__ void __launch_bounds__(kSgThreads) staged_kernel(
     const float* __restrict__ u, int H, int W, int C, int band, int G, int slot_f, Taps tp,
     const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
-    double inv_m, double* __restrict__ partials) {
+    double inv_m, float hd, double* __restrict__ partials) {
     extern __shared__ __align__(16) float sg[];
-    const float coef0 = GRAD ? (float)(2.0 * (double)(*gscalar) * inv_m) : 0.0f;
-    staged_body<HH, GRAD>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, partials, sg);
+    const float coef0 = GRAD ? grad_coef(gscalar, inv_m, hd) : 0.0f;
+    staged_body<HH, GRAD, HUBER>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, hd, partials, sg);
 }
 
 // Fixed-order sum of the per-CTA partials (one CTA, fixed tree).
@@ -444,8 +368,9 @@ static int check_args(const float* x, int H, int W, int C, float sigma, int ksiz
         return PLAS_ERR_INVALID_ARG;
     }
     if (!(sigma > 0.0f)) { plas::set_last_error("sigma must be > 0"); return PLAS_ERR_INVALID_ARG; }
-    // the shared-memory strip kernel (ksize > 15) holds 32 + 2h cells x C channels
-    if (ksize / 2 > kStreamMaxH && smem_bytes(C, ksize / 2) > 200 * 1024) {
+    // the shared-memory strip kernel (ksize > 15, or C > 256) holds 32 + 2h
+    // cells x C channels
+    if ((ksize / 2 > kStreamMaxH || C > kSgThreads) && smem_bytes(C, ksize / 2) > 200 * 1024) {
         plas::set_last_error("too many channels");
         return PLAS_ERR_INVALID_ARG;
     }
@@ -469,11 +394,8 @@ static dim3 grid_of(int H, int W) { return dim3((W + kTX - 1) / kTX, (H + kTYS -
 
 // Partial sums of either kernel for any ksize (the larger of the two counts).
 static size_t partial_bytes(int H, int W, int C) {
-    const long long nthr = (long long)((W + kXB - 1) / kXB) * C;
-    const long long gx = (nthr + kStreamThreads - 1) / kStreamThreads;
-    const long long n_stream = gx * ((H + 31) / 32);
     const dim3 g = grid_of(H, W);
-    long long n = std::max<long long>(n_stream, (long long)g.x * g.y);
+    long long n = (long long)g.x * g.y;
     if (C <= kSgThreads) {
         const int G = kSgThreads / C;
         n = std::max<long long>(n, (long long)((W + kSgCells * G - 1) / (kSgCells * G)) * ((H + 31) / 32));
@@ -494,11 +416,10 @@ static bool set_smem_attr(size_t bytes) {
                                 (int)bytes) == cudaSuccess;
 }
 
-// Launch plan of one pass: the streaming kernel for h <= 7 (band rows per CTA
-// chosen so that the grid has at most max_partials CTAs), else the
-// shared-memory strip kernel.
+// Launch plan of one pass: the staged kernel for h <= 7, C <= 256 and a
+// 16-byte aligned input (row bands chosen so that the grid has at most
+// max_partials CTAs), else the shared-memory strip kernel.
 struct Plan {
-    bool stream = false;
     bool staged = false;
     dim3 grid;
     int band = 0;
@@ -508,7 +429,6 @@ struct Plan {
 };
 
 constexpr size_t kSgMaxSmem = 160 * 1024;
-
 
 static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_partials) {
     Plan p;
@@ -531,95 +451,63 @@ static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_p
             return p;
         }
     }
-    if (h <= kStreamMaxH) {
-        const long long nthr = (long long)((W + kXB - 1) / kXB) * C;
-        const long long gx = (nthr + kStreamThreads - 1) / kStreamThreads;
-        int band = 32;
-        while ((long long)gx * ((H + band - 1) / band) > max_partials && band < H) band *= 2;
-        if (gx <= 0x7fffffffLL && gx * ((H + band - 1) / band) <= max_partials) {
-            p.stream = true;
-            p.band = band;
-            p.grid = dim3((unsigned)gx, (unsigned)((H + band - 1) / band));
-            p.partials = gx * ((H + band - 1) / band);
-            return p;
-        }
-    }
     p.grid = grid_of(H, W);
     p.smem = smem_bytes(C, h);
     p.partials = (long long)p.grid.x * p.grid.y;
     return p;
 }
 
-template <int HH>
-static int launch_staged(bool grad, const Plan& p, const float* u, int H, int W, int C,
-                         const Taps& tp, const float* lam, float* out, const float* g,
-                         double inv_m, double* partials, cudaStream_t st) {
-    if (p.smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(staged_kernel<HH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p.smem) != cudaSuccess ||
-            cudaFuncSetAttribute(staged_kernel<HH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p.smem) != cudaSuccess)
-            return PLAS_ERR_INVALID_ARG;
-    }
-    if (grad)
-        staged_kernel<HH, true><<<p.grid, kSgThreads, p.smem, st>>>(u, H, W, C, p.band, p.G, p.slot_f,
-                                                                    tp, lam, out, g, inv_m, partials);
-    else
-        staged_kernel<HH, false><<<p.grid, kSgThreads, p.smem, st>>>(u, H, W, C, p.band, p.G, p.slot_f,
-                                                                     tp, lam, out, g, inv_m, partials);
+template <int HH, bool GRAD, bool HUBER>
+static int launch_staged_t(const Plan& p, const float* u, int H, int W, int C, const Taps& tp,
+                           const float* lam, float* out, const float* g, double inv_m, float hd,
+                           double* partials, cudaStream_t st) {
+    if (p.smem > 48 * 1024 &&
+        cudaFuncSetAttribute(staged_kernel<HH, GRAD, HUBER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)p.smem) != cudaSuccess)
+        return PLAS_ERR_INVALID_ARG;
+    staged_kernel<HH, GRAD, HUBER><<<p.grid, kSgThreads, p.smem, st>>>(
+        u, H, W, C, p.band, p.G, p.slot_f, tp, lam, out, g, inv_m, hd, partials);
     return PLAS_OK;
 }
 
+// The gradient pass has no penalty-specific work (its scale is read from hd),
+// so it needs no Huber variant.
 template <int HH>
-static void launch_stream(bool grad, const Plan& p, const float* u, int H, int W, int C,
-                          const Taps& tp, const float* lam, float* out, const float* g,
-                          double inv_m, double* partials, cudaStream_t st) {
-    if (grad)
-        stream_kernel<HH, true><<<p.grid, kStreamThreads, 0, st>>>(u, H, W, C, p.band, tp, lam, out,
-                                                                   g, inv_m, partials);
-    else
-        stream_kernel<HH, false><<<p.grid, kStreamThreads, 0, st>>>(u, H, W, C, p.band, tp, lam,
-                                                                    out, g, inv_m, partials);
+static int launch_staged(bool grad, const Plan& p, const float* u, int H, int W, int C,
+                         const Taps& tp, const float* lam, float* out, const float* g,
+                         double inv_m, float hd, double* partials, cudaStream_t st) {
+    if (grad) return launch_staged_t<HH, true, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    if (hd > 0.0f)
+        return launch_staged_t<HH, false, true>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    return launch_staged_t<HH, false, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
 }
 
-// v = u - B u over the grid (GRAD: out = (2 g / M) lam v; else out = v if
-// given, and the per-CTA weighted sums of v^2 into partials).
+// v = u - B u over the grid (GRAD: out = coef lam v, coef = 2 g / M or g / M
+// for Huber; else out = v (clamped for Huber) if given, and the per-CTA
+// weighted sums of the penalty of v into partials).
 static int run_pass(bool grad, const Plan& p, const float* u, int H, int W, int C, int h,
                     const Taps& tp, const float* lam, float* out, const float* g, double inv_m,
-                    double* partials, cudaStream_t st) {
+                    float hd, double* partials, cudaStream_t st) {
     if (p.staged) {
         switch (h) {
-            case 0: return launch_staged<0>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 1: return launch_staged<1>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 2: return launch_staged<2>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 3: return launch_staged<3>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 4: return launch_staged<4>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 5: return launch_staged<5>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            case 6: return launch_staged<6>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
-            default: return launch_staged<7>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st);
+            case 0: return launch_staged<0>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 1: return launch_staged<1>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 2: return launch_staged<2>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 3: return launch_staged<3>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 4: return launch_staged<4>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 5: return launch_staged<5>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            case 6: return launch_staged<6>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+            default: return launch_staged<7>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
         }
-    }
-    if (p.stream) {
-        switch (h) {
-            case 0: launch_stream<0>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 1: launch_stream<1>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 2: launch_stream<2>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 3: launch_stream<3>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 4: launch_stream<4>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 5: launch_stream<5>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            case 6: launch_stream<6>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-            default: launch_stream<7>(grad, p, u, H, W, C, tp, lam, out, g, inv_m, partials, st); break;
-        }
-        return PLAS_OK;
     }
     if (grad) {
         if (!set_smem_attr<true>(p.smem)) return PLAS_ERR_INVALID_ARG;
         smooth_kernel<true><<<p.grid, kThreads, p.smem, st>>>(u, H, W, C, h, tp, lam, out, g, inv_m,
-                                                              partials);
+                                                              hd, partials);
     } else {
         if (!set_smem_attr<false>(p.smem)) return PLAS_ERR_INVALID_ARG;
         smooth_kernel<false><<<p.grid, kThreads, p.smem, st>>>(u, H, W, C, h, tp, lam, out, g,
-                                                               inv_m, partials);
+                                                               inv_m, hd, partials);
     }
     return PLAS_OK;
 }
@@ -666,10 +554,14 @@ size_t plas_smooth_loss_workspace_bytes(int H, int W, int C) {
     return ws_bytes_for(H, W, C);
 }
 
-int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int ksize,
-                         const float* ch_weights, float* loss, void* workspace, size_t ws_bytes,
-                         void* stream) {
+int plas_smooth_loss_fwd_ex(const float* x, int H, int W, int C, float sigma, int ksize,
+                            const float* ch_weights, float huber_delta, float* loss,
+                            void* workspace, size_t ws_bytes, void* stream) {
     if (int e = check_args(x, H, W, C, sigma, ksize)) return e;
+    if (!(huber_delta >= 0.0f) || huber_delta > 3.0e38f) {
+        plas::set_last_error("huber_delta must be finite and >= 0");
+        return PLAS_ERR_INVALID_ARG;
+    }
     if (!loss) { plas::set_last_error("loss is NULL"); return PLAS_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     const int h = ksize / 2;
@@ -688,7 +580,7 @@ int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int k
     }
     const double inv_m = 1.0 / ((double)H * W * C);
     int rc = run_pass(false, p, x, H, W, C, h, make_taps(sigma, ksize), ch_weights, nullptr, nullptr,
-                      inv_m, (double*)mem, st);
+                      inv_m, huber_delta, (double*)mem, st);
     if (rc == PLAS_OK)
         finish_loss_kernel<<<1, 1024, 0, st>>>((const double*)mem, (int)p.partials, inv_m, loss);
     cudaError_t e = cudaGetLastError();
@@ -704,10 +596,14 @@ int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int k
     return PLAS_OK;
 }
 
-int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int ksize,
-                         const float* ch_weights, const float* grad_loss, float* grad_x,
-                         void* workspace, size_t ws_bytes, void* stream) {
+int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, int ksize,
+                            const float* ch_weights, float huber_delta, const float* grad_loss,
+                            float* grad_x, void* workspace, size_t ws_bytes, void* stream) {
     if (int e = check_args(x, H, W, C, sigma, ksize)) return e;
+    if (!(huber_delta >= 0.0f) || huber_delta > 3.0e38f) {
+        plas::set_last_error("huber_delta must be finite and >= 0");
+        return PLAS_ERR_INVALID_ARG;
+    }
     if (!grad_loss || !grad_x) { plas::set_last_error("grad_loss / grad_x is NULL"); return PLAS_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t need = ws_bytes_for(H, W, C);
@@ -727,11 +623,14 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
     const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
     const double inv_m = 1.0 / ((double)H * W * C);
     const Taps tp = make_taps(sigma, ksize);
-    // pass 1: r = x - B x (the weighted residual sums are a by-product)
-    int rc = run_pass(false, p, x, H, W, C, h, tp, ch_weights, r, nullptr, inv_m, (double*)mem, st);
-    // pass 2: grad = (2 g / M) lam (r - B r)
+    // pass 1: r = x - B x (clamped to [-delta, delta] for Huber); the
+    // weighted penalty sums are a by-product
+    int rc = run_pass(false, p, x, H, W, C, h, tp, ch_weights, r, nullptr, inv_m, huber_delta,
+                      (double*)mem, st);
+    // pass 2: grad = coef lam (r - B r), coef = 2 g / M (squared) or g / M (Huber)
     if (rc == PLAS_OK)
-        rc = run_pass(true, p, r, H, W, C, h, tp, ch_weights, grad_x, grad_loss, inv_m, nullptr, st);
+        rc = run_pass(true, p, r, H, W, C, h, tp, ch_weights, grad_x, grad_loss, inv_m, huber_delta,
+                      nullptr, st);
     cudaError_t e = cudaGetLastError();
     if (!workspace) cudaFreeAsync(mem, st);
     if (rc != PLAS_OK) {
@@ -743,6 +642,20 @@ int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int k
         return PLAS_ERR_CUDA;
     }
     return PLAS_OK;
+}
+
+int plas_smooth_loss_fwd(const float* x, int H, int W, int C, float sigma, int ksize,
+                         const float* ch_weights, float* loss, void* workspace, size_t ws_bytes,
+                         void* stream) {
+    return plas_smooth_loss_fwd_ex(x, H, W, C, sigma, ksize, ch_weights, 0.0f, loss, workspace,
+                                   ws_bytes, stream);
+}
+
+int plas_smooth_loss_bwd(const float* x, int H, int W, int C, float sigma, int ksize,
+                         const float* ch_weights, const float* grad_loss, float* grad_x,
+                         void* workspace, size_t ws_bytes, void* stream) {
+    return plas_smooth_loss_bwd_ex(x, H, W, C, sigma, ksize, ch_weights, 0.0f, grad_loss, grad_x,
+                                   workspace, ws_bytes, stream);
 }
 
 // Same result as plas_smooth_loss_fwd; allocates nothing (see plas.h).
@@ -769,7 +682,7 @@ int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigm
     const double inv_m = 1.0 / ((double)H * W * C);
     // every CTA writes its own partial, so the array needs no clearing
     int rc = run_pass(false, p, x, H, W, C, h, make_taps(sigma, ksize), ch_weights, nullptr, nullptr,
-                      inv_m, partials, st);
+                      inv_m, 0.0f, partials, st);
     if (rc != PLAS_OK) {
         cudaGetLastError();
         plas::set_last_error("too many channels for the shared-memory tile");

@@ -68,6 +68,17 @@ def loss_grid(H: int, W: int, seed: int = 0) -> np.ndarray:
     return np.concatenate([x, c], axis=1).reshape(H, W, SORT_CHANNELS + CARRIED_CHANNELS)
 
 
+def paper_smoothness_weights() -> np.ndarray:
+    """Per-channel smoothness-loss weights of the paper's configuration
+    (supplementary, Tab. "params": opacity 0.09, rotation 0.91, the other
+    attributes 0) for the 59-channel layout of loss_grid: xyz 0-2, scale
+    3-5, rotation 6-9, opacity 10, DC colour 11-13, SH rest 14-58."""
+    lam = np.zeros(SORT_CHANNELS + CARRIED_CHANNELS, np.float32)
+    lam[6:10] = 0.91
+    lam[10] = 0.09
+    return lam
+
+
 def request_stream(n: int = 64, seed: int = 0, side_lo: int = 128, side_hi: int = 1024,
                    rate_per_s: float = 10.0):
     """n requests: (arrival time in s, grid side); exponential inter-arrivals."""

@@ -99,3 +99,44 @@ def test_loss_in_training_loop_with_resorts(plas, orc):
         opt.step()
         losses.append(loss.item())
     assert losses[-1] < losses[0]
+
+
+@pytest.mark.parametrize("H,W,C,sigma,ksize,delta", [(40, 36, 5, 1.0, 7, 0.05), (64, 64, 59, 3.0, 5, 1.0),
+                                                      (33, 70, 14, 3.0, 5, 0.02), (8, 200, 2, 2.0, 31, 0.1)])
+def test_huber_loss_matches_fp64(plas, orc, H, W, C, sigma, ksize, delta):
+    """Huber form (Sec. 3.2) on the staged kernel and (ksize 31) the strip
+    kernel: loss within 1e-5 of FP64, gradient within 1e-5 in norm and max."""
+    x = (np.random.default_rng(H * W + C).random((H, W, C), dtype=np.float32) * 2.0)
+    lam = (np.random.default_rng(2).random(C) + 0.5).astype(np.float32)
+    xc = torch.from_numpy(x).cuda().requires_grad_(True)
+    L = plas.smooth_loss(xc, sigma, ksize, torch.from_numpy(lam).cuda(), huber_delta=delta)
+    (L * 0.6).backward()
+    L64, g64 = orc.smooth_loss64(x, sigma, ksize, lam, grad_loss=0.6, huber_delta=delta)
+    assert abs(L.item() - L64) <= 1e-5 * abs(L64)
+    gg = xc.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g64) <= 1e-5 * np.linalg.norm(g64)
+    assert np.abs(gg - g64).max() <= 1e-5 * np.abs(g64).max()
+
+
+def test_huber_paper_configuration_full_size(plas, orc):
+    """The paper's regulariser settings (kernel 5, sigma 3, weights 0.09 on
+    opacity and 0.91 on rotation, delta 1) on the 1024x1024x59 grid."""
+    x = synth.loss_grid(1024, 1024, seed=1).astype(np.float32)
+    lam = synth.paper_smoothness_weights()
+    xc = torch.from_numpy(x).cuda().requires_grad_(True)
+    L = plas.smooth_loss(xc, 3.0, 5, torch.from_numpy(lam).cuda(), huber_delta=1.0)
+    L.backward()
+    L64, g64 = orc.smooth_loss64(x, 3.0, 5, lam, huber_delta=1.0)
+    assert abs(L.item() - L64) <= 1e-5 * abs(L64)
+    gg = xc.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g64) <= 1e-5 * np.linalg.norm(g64)
+    assert np.abs(gg - g64).max() <= 1e-5 * np.abs(g64).max()
+    assert np.all(gg[..., lam == 0] == 0.0)
+
+
+def test_huber_rejects_bad_delta(plas):
+    x = torch.rand(16, 16, 3, device="cuda")
+    with pytest.raises(RuntimeError):
+        plas.smooth_loss_fwd(x, 1.0, 7, huber_delta=float("nan"))
+    with pytest.raises(RuntimeError):
+        plas.smooth_loss_fwd(x, 1.0, 7, huber_delta=-1.0)
