@@ -179,7 +179,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // iteration (the blurred row and the centre row h rows above it)
 __host__ __device__ constexpr int sg_slots(int h) { return kSgAhead + h + 2; }
 
-template <int HH, bool GRAD, bool HUBER>
+template <int HH, bool GRAD, bool HUBER, bool WRITE>
 __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, int W, int C,
                                             int band, int G, int slot_f, const Taps& tp,
                                             const float* __restrict__ lam, float* __restrict__ out,
@@ -201,6 +201,16 @@ __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, 
     const int xg = x0 + kSgCells * g;
     const bool ok = g < G && xg < W;
     const int soff = ok ? kSgCells * g * C + c : 0;  // unused threads read in-bounds
+    // cells of the pair (i, i + 4) that are inside the grid (branch-free
+    // masks; the staged row already holds zeros beyond the grid)
+    bool va[NP], vb[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        va[i] = ok && xg + i < W;
+        vb[i] = ok && xg + i + NP < W;
+    }
+    // output pointer of this thread's channel at cell xg of row 0
+    float* const obase = (GRAD || WRITE) ? out + (long long)xg * C + c : nullptr;
     const float l = (lam && ok) ? __ldg(lam + c) : 1.0f;
     const float2 coef2 = GRAD ? make_float2(__fmul_rn(coef0, l), __fmul_rn(coef0, l))
                               : make_float2(0.0f, 0.0f);
@@ -283,24 +293,20 @@ __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, 
                         // centre - blur, one rounding (FMA with -1)
                         const float2 vv = __ffma2_rn(make_float2(-1.0f, -1.0f), acc,
                                                      make_float2(rc[i * C], rc[(i + NP) * C]));
-                        if (ok) {
-                            const int xa = xg + i, xb = xg + i + NP;
-                            const long long o = (long long)yc * WC + (long long)xa * C + c;
-                            if (GRAD) {
-                                const float2 gv = __fmul2_rn(coef2, vv);
-                                if (xa < W) out[o] = gv.x;
-                                if (xb < W) out[o + NP * C] = gv.y;
-                            } else {
-                                if (out) {
-                                    if (xa < W) out[o] = HUBER ? resid_out(vv.x, hd) : vv.x;
-                                    if (xb < W) out[o + NP * C] = HUBER ? resid_out(vv.y, hd) : vv.y;
-                                }
-                                const float2 m2 = make_float2(xa < W ? vv.x : 0.0f, xb < W ? vv.y : 0.0f);
-                                if (HUBER)
-                                    sq = __fadd2_rn(sq, make_float2(loss_term(m2.x, hd), loss_term(m2.y, hd)));
-                                else
-                                    sq = __ffma2_rn(m2, m2, sq);
-                            }
+                        if (GRAD || WRITE) {
+                            float* o = obase + (long long)yc * WC + (long long)i * C;
+                            float2 w = vv;
+                            if (GRAD) w = __fmul2_rn(coef2, vv);
+                            else if (HUBER) w = make_float2(resid_out(vv.x, hd), resid_out(vv.y, hd));
+                            if (va[i]) o[0] = w.x;
+                            if (vb[i]) o[NP * C] = w.y;
+                        }
+                        if (!GRAD) {
+                            const float2 m2 = make_float2(va[i] ? vv.x : 0.0f, vb[i] ? vv.y : 0.0f);
+                            if (HUBER)
+                                sq = __fadd2_rn(sq, make_float2(loss_term(m2.x, hd), loss_term(m2.y, hd)));
+                            else
+                                sq = __ffma2_rn(m2, m2, sq);
                         }
                     }
                     if (!GRAD) band_acc = __ffma2_rn(make_float2(l, l), sq, band_acc);
@@ -331,14 +337,15 @@ __device__ __forceinline__ void staged_body(const float* __restrict__ u, int H, 
     }
 }
 
-template <int HH, bool GRAD, bool HUBER>
+template <int HH, bool GRAD, bool HUBER, bool WRITE>
 __global__ void __launch_bounds__(kSgThreads) staged_kernel(
     const float* __restrict__ u, int H, int W, int C, int band, int G, int slot_f, Taps tp,
     const float* __restrict__ lam, float* __restrict__ out, const float* __restrict__ gscalar,
     double inv_m, float hd, double* __restrict__ partials) {
     extern __shared__ __align__(16) float sg[];
     const float coef0 = GRAD ? grad_coef(gscalar, inv_m, hd) : 0.0f;
-    staged_body<HH, GRAD, HUBER>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, hd, partials, sg);
+    staged_body<HH, GRAD, HUBER, WRITE>(u, H, W, C, band, G, slot_f, tp, lam, out, coef0, hd, partials,
+                                        sg);
 }
 
 // Fixed-order sum of the per-CTA partials (one CTA, fixed tree).
@@ -457,15 +464,15 @@ static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_p
     return p;
 }
 
-template <int HH, bool GRAD, bool HUBER>
+template <int HH, bool GRAD, bool HUBER, bool WRITE>
 static int launch_staged_t(const Plan& p, const float* u, int H, int W, int C, const Taps& tp,
                            const float* lam, float* out, const float* g, double inv_m, float hd,
                            double* partials, cudaStream_t st) {
     if (p.smem > 48 * 1024 &&
-        cudaFuncSetAttribute(staged_kernel<HH, GRAD, HUBER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p.smem) != cudaSuccess)
+        cudaFuncSetAttribute(staged_kernel<HH, GRAD, HUBER, WRITE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess)
         return PLAS_ERR_INVALID_ARG;
-    staged_kernel<HH, GRAD, HUBER><<<p.grid, kSgThreads, p.smem, st>>>(
+    staged_kernel<HH, GRAD, HUBER, WRITE><<<p.grid, kSgThreads, p.smem, st>>>(
         u, H, W, C, p.band, p.G, p.slot_f, tp, lam, out, g, inv_m, hd, partials);
     return PLAS_OK;
 }
@@ -476,10 +483,16 @@ template <int HH>
 static int launch_staged(bool grad, const Plan& p, const float* u, int H, int W, int C,
                          const Taps& tp, const float* lam, float* out, const float* g,
                          double inv_m, float hd, double* partials, cudaStream_t st) {
-    if (grad) return launch_staged_t<HH, true, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
-    if (hd > 0.0f)
-        return launch_staged_t<HH, false, true>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
-    return launch_staged_t<HH, false, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    if (grad)
+        return launch_staged_t<HH, true, false, true>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    if (hd > 0.0f) {
+        if (out)
+            return launch_staged_t<HH, false, true, true>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+        return launch_staged_t<HH, false, true, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    }
+    if (out)
+        return launch_staged_t<HH, false, false, true>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
+    return launch_staged_t<HH, false, false, false>(p, u, H, W, C, tp, lam, out, g, inv_m, hd, partials, st);
 }
 
 // v = u - B u over the grid (GRAD: out = coef lam v, coef = 2 g / M or g / M
