@@ -202,6 +202,15 @@ int plas_sort(const float* x, int H, int W, int D, const float* weights,
  * float32 (must not overlap); perm: device N int32 with values in [0, N)
  * (not checked).  C >= 1.
  */
+/*
+ * plas_select_rows -- dst[p, :] = src[idx[p], :] for p < n_out, from a
+ * source of n_src rows (the kept Gaussians of plas_grid_select, or any
+ * subset).  Entries of idx outside [0, n_src) give zero rows.  src: device
+ * n_src x C float32, dst: device n_out x C float32 (no overlap), idx: device
+ * n_out int32.  C >= 1.
+ */
+int plas_select_rows(const float* src, long long n_src, int C, const int32_t* idx,
+                     long long n_out, float* dst, void* stream);
 int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float* dst,
                      void* stream);
 
@@ -314,6 +323,34 @@ int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, in
  */
 int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigma, int ksize,
                                  const float* ch_weights, float* loss, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* preparation of 3DGS attributes before the sort (Sec. 3.1, Sec. 3.3)     */
+/* ---------------------------------------------------------------------- */
+/*
+ * plas_activate_3dgs -- the sort runs on activated values (Sec. 3.1).  Row
+ * i of raw (stride floats apart, stride >= 14) holds the trained parameters
+ * xyz 0-2 (contracted, Sec. 3.3 "Coordinate space contraction"), log-scale
+ * 3-5, quaternion 6-9, opacity logit 10, DC colour 11-13.  out (device,
+ * N x 14) receives
+ *   xyz = sign(v) * (exp(|v|) - 1), scale = exp(v), quaternion / |q| (a zero
+ *   quaternion stays zero), opacity = 1 / (1 + exp(-v)), DC as stored,
+ * in FP32 with the CUDA math library (within a few ulp of the FP64 values).
+ *
+ * plas_grid_select -- the largest square grid the Gaussians fill (Sec.
+ * 3.1): side = floor(sqrt(N)), written to *side_out (host).  keep (device,
+ * side^2 int32) receives the indices of the side^2 Gaussians with the
+ * highest opacity logit, in ascending index order.  Ties go to the lower
+ * index, -0 reads as +0, and NaN ranks lowest.  The rest are pruned.
+ * 'opacity' points at the first logit, 'stride' floats apart (14 for the raw
+ * layout above, from raw + 10).  workspace: device or NULL,
+ * plas_grid_select_workspace_bytes(N) bytes, 256-byte aligned.  N < 2^31.
+ * Errors: PLAS_ERR_INVALID_ARG, PLAS_ERR_OOM, PLAS_ERR_CUDA.
+ */
+int plas_activate_3dgs(const float* raw, long long N, int stride, float* out, void* stream);
+size_t plas_grid_select_workspace_bytes(long long N);
+int plas_grid_select(const float* opacity, long long N, int stride, int32_t* keep, int* side_out,
+                     void* workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* quantisation of the sorted attribute grids (Sec. 3.3)                   */

@@ -118,6 +118,9 @@ def lib():
             L.orc_smooth_loss64.restype = d
             L.orc_smooth_loss64_huber.argtypes = [P(d), i, i, i, d, i, P(d), d, d, P(d)]
             L.orc_smooth_loss64_huber.restype = d
+            L.orc_activate_3dgs.argtypes = [f, ctypes.c_long, i, f]
+            L.orc_grid_select.argtypes = [f, ctypes.c_long, i, P(i)]
+            L.orc_grid_select.restype = i
             L.orc_quantize.argtypes = [f, ctypes.c_long, i, f, f, P(i),
                                        P(ctypes.c_ushort)]
             L.orc_num_threads.restype = i
@@ -309,6 +312,24 @@ def smooth_loss64(x: np.ndarray, sigma: float = 1.0, ksize: int = 7, lam=None,
         L = lib().orc_smooth_loss64(_p(x, ctypes.c_double), H, W, C, sigma, ksize,
                                     _p(lam, ctypes.c_double), grad_loss, _p(g, ctypes.c_double))
     return L, g
+
+
+def activate_3dgs(raw: np.ndarray) -> np.ndarray:
+    """Activated sort features [N, 14] of raw 3DGS parameters [N, >=14]."""
+    raw = _f32(raw)
+    n, stride = raw.shape
+    out = np.zeros((n, 14), np.float32)
+    lib().orc_activate_3dgs(_p(raw, ctypes.c_float), n, stride, _p(out, ctypes.c_float))
+    return out
+
+
+def grid_select(opacity_logit: np.ndarray):
+    """(side, keep) of the largest square grid, keeping the highest opacities."""
+    op = _f32(opacity_logit)
+    n = op.shape[0]
+    keep = np.zeros(max(n, 1), np.int32)
+    side = lib().orc_grid_select(_p(op, ctypes.c_float), n, 1, _p(keep, ctypes.c_int))
+    return side, keep[:side * side].copy()
 
 
 def quantize(x: np.ndarray, lo, hi, q) -> np.ndarray:

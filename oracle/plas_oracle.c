@@ -745,6 +745,68 @@ void orc_quantize(const float* x, long n, int C, const float* lo, const float* h
     }
 }
 
+/* Activation of raw 3DGS parameters into the sort features (Sec. 3.1: the
+ * sort uses the values the renderer sees; Sec. 3.3: coordinates go through
+ * x = sign(v) (exp(|v|) - 1)).  Row layout of raw (stride floats apart):
+ * xyz 0-2, log-scale 3-5, quaternion 6-9, opacity logit 10, DC 11-13.
+ * Evaluated in FP64 and rounded once to FP32. */
+void orc_activate_3dgs(const float* raw, long n, int stride, float* out)
+{
+    for (long i = 0; i < n; ++i) {
+        const float* r = raw + i * stride;
+        float* o = out + i * 14;
+        for (int k = 0; k < 3; ++k) {
+            const double v = r[k];
+            const double m = exp(fabs(v)) - 1.0;
+            o[k] = (float)(v < 0 ? -m : m);
+        }
+        for (int k = 3; k < 6; ++k) o[k] = (float)exp((double)r[k]);
+        double nn = 0.0;
+        for (int k = 6; k < 10; ++k) nn += (double)r[k] * (double)r[k];
+        nn = sqrt(nn);
+        for (int k = 6; k < 10; ++k) o[k] = nn > 0 ? (float)((double)r[k] / nn) : 0.0f;
+        o[10] = (float)(1.0 / (1.0 + exp(-(double)r[10])));
+        for (int k = 11; k < 14; ++k) o[k] = r[k];
+    }
+}
+
+/* Largest square grid that the Gaussians fill (Sec. 3.1: the ones with the
+ * lowest opacity that do not fit are pruned): side = floor(sqrt(n)); keep
+ * receives the side^2 indices with the largest opacity logits (ties to the
+ * lower index; -0 equals +0; NaN ranks lowest), in ascending index order.
+ * Written as a plain sort.  Returns side. */
+static const float* g_sel_op;
+static long g_sel_stride;
+static int sel_cmp(const void* a, const void* b)
+{
+    const long i = *(const long*)a, j = *(const long*)b;
+    const float x = g_sel_op[i * g_sel_stride], y = g_sel_op[j * g_sel_stride];
+    const int xn = x != x, yn = y != y;
+    if (xn != yn) return xn ? 1 : -1;         /* NaN last */
+    if (!xn && x != y) return x > y ? -1 : 1; /* larger logit first (-0 == +0) */
+    return i < j ? -1 : (i > j ? 1 : 0);      /* then the lower index */
+}
+static int idx_cmp(const void* a, const void* b)
+{
+    const long i = *(const long*)a, j = *(const long*)b;
+    return i < j ? -1 : (i > j ? 1 : 0);
+}
+int orc_grid_select(const float* opacity, long n, int stride, int* keep)
+{
+    long side = (long)floor(sqrt((double)n));
+    while (side * side > n) --side;
+    while ((side + 1) * (side + 1) <= n) ++side;
+    long* idx = (long*)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) idx[i] = i;
+    g_sel_op = opacity;
+    g_sel_stride = stride;
+    qsort(idx, (size_t)n, sizeof(long), sel_cmp);
+    qsort(idx, (size_t)(side * side), sizeof(long), idx_cmp);
+    for (long i = 0; i < side * side; ++i) keep[i] = (int)idx[i];
+    free(idx);
+    return (int)side;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

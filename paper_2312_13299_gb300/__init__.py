@@ -16,6 +16,7 @@ Main entry points
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass, field, fields
 from typing import Optional, Sequence
 
@@ -381,6 +382,19 @@ def gather_rows(src: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
     return out.reshape(src.shape)
 
 
+def select_rows(src: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
+    """out[p] = src[idx[p]] for a subset of rows (e.g. the kept Gaussians)."""
+    src = _need_cuda(src, "src")
+    idx = _need_cuda(idx, "idx", torch.int32)
+    src2 = src.reshape(src.shape[0], -1)
+    out = torch.empty((idx.numel(), src2.shape[1]), dtype=torch.float32, device=src.device)
+    with torch.cuda.device(src.device):
+        rc = load().plas_select_rows(src2.data_ptr(), src2.shape[0], src2.shape[1], idx.data_ptr(),
+                                     idx.numel(), out.data_ptr(), _stream(src.device))
+    check(rc, "plas_select_rows")
+    return out.reshape((idx.numel(),) + tuple(src.shape[1:]))
+
+
 def target(x: torch.Tensor, H: int, W: int, perm: torch.Tensor, phi: float, weights=None,
            normalize: bool = True, sigma_ratio: float = 2.0) -> torch.Tensor:
     """Low-pass target of one arrangement (the blur step of Sec. 3.1) -> [H, W, D]."""
@@ -428,6 +442,39 @@ def grid_metrics(grid: torch.Tensor, scale: float = 1.0):
                                       _stream(grid.device))
     check(rc, "plas_grid_metrics")
     return out[0], out[1], out[2]
+
+
+def activate_3dgs(raw: torch.Tensor) -> torch.Tensor:
+    """Raw 3DGS parameters [N, >=14] (contracted xyz, log-scale, quaternion,
+    opacity logit, DC) -> activated sort features [N, 14] (Sec. 3.1)."""
+    raw = _need_cuda(raw, "raw")
+    if raw.dim() != 2 or raw.shape[1] < 14 or raw.stride(1) != 1:
+        raise ValueError("raw must be [N, >=14] with unit column stride")
+    out = torch.empty((raw.shape[0], 14), dtype=torch.float32, device=raw.device)
+    with torch.cuda.device(raw.device):
+        rc = load().plas_activate_3dgs(raw.data_ptr(), raw.shape[0], raw.stride(0), out.data_ptr(),
+                                       _stream(raw.device))
+    check(rc, "plas_activate_3dgs")
+    return out
+
+
+def grid_select(opacity_logit: torch.Tensor):
+    """Largest square grid (Sec. 3.1): returns (side, keep) with keep the
+    int32 indices of the side^2 highest-opacity Gaussians, ascending.
+    opacity_logit: a 1-D CUDA float32 tensor (any element stride)."""
+    op = opacity_logit
+    if not isinstance(op, torch.Tensor) or not op.is_cuda or op.dtype != torch.float32 or op.dim() != 1:
+        raise ValueError("opacity_logit must be a 1-D float32 CUDA tensor")
+    n = op.shape[0]
+    side = math.isqrt(n)
+    keep = torch.empty(side * side, dtype=torch.int32, device=op.device)
+    s = ctypes.c_int()
+    with torch.cuda.device(op.device):
+        rc = load().plas_grid_select(op.data_ptr(), n, op.stride(0), keep.data_ptr(), ctypes.byref(s),
+                                     None, 0, _stream(op.device))
+    check(rc, "plas_grid_select")
+    assert s.value == side
+    return side, keep
 
 
 def _quant_args(C, lo, hi, q):

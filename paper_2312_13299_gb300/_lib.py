@@ -85,6 +85,7 @@ SIGNATURES = {
     "plas_sort": (c_int, [c_void_p, c_int, c_int, c_int, P(c_float), c_void_p, c_int, c_uint64,
                           P(plas_schedule), c_void_p, P(plas_state), c_void_p, c_void_p,
                           c_void_p, c_void_p, c_size_t, P(plas_stats), c_void_p]),
+    "plas_select_rows": (c_int, [c_void_p, c_ll, c_int, c_void_p, c_ll, c_void_p, c_void_p]),
     "plas_gather_rows": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "plas_target": (c_int, [c_void_p, c_int, c_int, c_int, P(c_float), c_int, c_void_p,
                             c_double, c_double, c_void_p, c_void_p]),
@@ -104,6 +105,10 @@ SIGNATURES = {
                                         c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "plas_smooth_loss_fwd_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int,
                                              c_void_p, c_void_p, c_void_p]),
+    "plas_activate_3dgs": (c_int, [c_void_p, c_ll, c_int, c_void_p, c_void_p]),
+    "plas_grid_select_workspace_bytes": (c_size_t, [c_ll]),
+    "plas_grid_select": (c_int, [c_void_p, c_ll, c_int, c_void_p, P(c_int), c_void_p, c_size_t,
+                                 c_void_p]),
     "plas_quantize": (c_int, [c_void_p, c_ll, c_int, P(c_float), P(c_float), P(c_int), c_void_p,
                               c_void_p]),
     "plas_dequantize": (c_int, [c_void_p, c_ll, c_int, P(c_float), P(c_float), P(c_int),

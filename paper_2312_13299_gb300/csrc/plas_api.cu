@@ -340,6 +340,16 @@ int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float*
     return check_launch("gather_rows");
 }
 
+int plas_select_rows(const float* src, long long n_src, int C, const int32_t* idx, long long n_out,
+                     float* dst, void* stream) {
+    g_last_error.clear();
+    if (n_src < 0 || n_out < 0 || C < 1) return fail(PLAS_ERR_INVALID_ARG, "sizes must be >= 0, C >= 1");
+    if (n_out == 0) return PLAS_OK;
+    if (!src || !idx || !dst) return fail(PLAS_ERR_INVALID_ARG, "NULL pointer");
+    launch_gather_rows(src, n_out, C, idx, dst, (cudaStream_t)stream, n_src);
+    return check_launch("select_rows");
+}
+
 int plas_target(const float* x, int H, int W, int D, const float* weights, int normalize,
                 const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream) {
     g_last_error.clear();

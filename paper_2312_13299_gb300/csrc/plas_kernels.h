@@ -114,9 +114,10 @@ void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, dou
 
 // ---- outputs -----------------------------------------------------------------
 void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream_t s);
-// Entries of perm outside [0, N) are not read; their rows are written as zeros.
+// dst[p] = src[perm[p]] for p < N; src has Nsrc rows (< 0: N).  Entries of
+// perm outside [0, Nsrc) are not read; their rows are written as zeros.
 void launch_gather_rows(const float* src, long long N, int C, const int32_t* perm, float* dst,
-                        cudaStream_t s);
+                        cudaStream_t s, long long Nsrc = -1);
 void launch_copy_features(const float* T, int N, int D, int ts, float* out, cudaStream_t s);
 // acc[0] sum of neighbour L2, acc[1] sum |diff|*scale, acc[2] sum (|diff|*scale)^2
 void launch_neighbour_metrics(const float* g, int stride, int H, int W, int D, double scale,

@@ -255,7 +255,7 @@ void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream
 }
 
 // dst[p, c] = src[perm[p], c]; consecutive threads write consecutive floats.
-__global__ void gather_rows_kernel(const float* __restrict__ src, long long N, int C,
+__global__ void gather_rows_kernel(const float* __restrict__ src, long long N, long long Nsrc, int C,
                                    const int32_t* __restrict__ perm, float* __restrict__ dst) {
     const long long total = N * C;
     for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
@@ -263,11 +263,11 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, long long N, i
         const long long p = o / C;
         const int c = (int)(o - p * C);
         const int q = __ldg(perm + p);
-        dst[o] = (q >= 0 && q < N) ? __ldg(src + (size_t)q * C + c) : 0.0f;
+        dst[o] = (q >= 0 && q < Nsrc) ? __ldg(src + (size_t)q * C + c) : 0.0f;
     }
 }
 
-__global__ void gather_rows4_kernel(const float4* __restrict__ src, long long N, int C4,
+__global__ void gather_rows4_kernel(const float4* __restrict__ src, long long N, long long Nsrc, int C4,
                                     const int32_t* __restrict__ perm, float4* __restrict__ dst) {
     const long long total = N * C4;
     for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
@@ -275,22 +275,23 @@ __global__ void gather_rows4_kernel(const float4* __restrict__ src, long long N,
         const long long p = o / C4;
         const int c = (int)(o - p * C4);
         const int q = __ldg(perm + p);
-        dst[o] = (q >= 0 && q < N) ? __ldg(src + (size_t)q * C4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[o] = (q >= 0 && q < Nsrc) ? __ldg(src + (size_t)q * C4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
 void launch_gather_rows(const float* src, long long N, int C, const int32_t* perm, float* dst,
-                        cudaStream_t s) {
+                        cudaStream_t s, long long Nsrc) {
     if (N <= 0 || C <= 0) return;
+    if (Nsrc < 0) Nsrc = N;
     const bool vec = (C % 4 == 0) &&
                      ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) % 16 == 0);
     const long long total = vec ? N * (C / 4) : N * C;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
     if (vec)
-        gather_rows4_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(src), N, C / 4,
-                                                   perm, reinterpret_cast<float4*>(dst));
+        gather_rows4_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(src), N, Nsrc,
+                                                   C / 4, perm, reinterpret_cast<float4*>(dst));
     else
-        gather_rows_kernel<<<blocks, 256, 0, s>>>(src, N, C, perm, dst);
+        gather_rows_kernel<<<blocks, 256, 0, s>>>(src, N, Nsrc, C, perm, dst);
 }
 
 __global__ void copy_features_kernel(const float* __restrict__ T, long long N, int D, int ts,
