@@ -53,7 +53,7 @@ class Schedule(ctypes.Structure):
                 ("phi_min", ctypes.c_double), ("tol", ctypes.c_double),
                 ("sigma_ratio", ctypes.c_double), ("min_block", ctypes.c_int),
                 ("shuffle_init", ctypes.c_int), ("normalize", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("max_iters", ctypes.c_longlong)]
+                ("target_mode", ctypes.c_int), ("max_iters", ctypes.c_longlong)]
 
 
 class State(ctypes.Structure):
@@ -72,7 +72,7 @@ def default_schedule(**kw) -> Schedule:
     """Defaults: phi0 = w/2-1, shrink 0.95, stop below 1 (Sec. 3.1); tol 1e-4
     (supplementary); min block 16 (Sec. 3.1); sigma = 2 phi (paper silent)."""
     s = Schedule(phi0=0.0, shrink=0.95, phi_min=1.0, tol=1e-4, sigma_ratio=2.0,
-                 min_block=16, shuffle_init=1, normalize=1, pad_=0, max_iters=0)
+                 min_block=16, shuffle_init=1, normalize=1, target_mode=0, max_iters=0)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -111,6 +111,9 @@ def lib():
                                    P(State), P(ctypes.c_int32), P(ll), P(i), ll, f]
             L.orc_sort.restype = ll
             L.orc_target.argtypes = [f, i, i, i, f, i, P(ctypes.c_int32), d, d, f]
+            L.orc_target_box.argtypes = [f, i, i, i, f, i, P(ctypes.c_int32), d, f]
+            L.orc_box_exp.argtypes = [f, ctypes.c_long, i, f, i]
+            L.orc_box_exp.restype = i
             L.orc_gather.argtypes = [f, ctypes.c_long, i, P(ctypes.c_int32), f]
             L.orc_metrics.argtypes = [f, i, i, i, d, P(d), P(d)]
             L.orc_smooth_taps64.argtypes = [d, i, P(d)]
@@ -269,6 +272,26 @@ def target(x: np.ndarray, H: int, W: int, perm, phi: float, weights=None,
     lib().orc_target(_p(x, ctypes.c_float), H, W, D, _p(w, ctypes.c_float), int(normalize_),
                      _p(p, ctypes.c_int32), phi, sigma_ratio, _p(T, ctypes.c_float))
     return T
+
+
+def target_box(x: np.ndarray, H: int, W: int, perm, phi: float, weights=None,
+               normalize_: bool = True) -> np.ndarray:
+    """Box target (fixed-point window mean) of one arrangement -> [H, W, D]."""
+    x = _f32(x).reshape(H * W, -1)
+    D = x.shape[1]
+    w = None if weights is None else _f32(weights)
+    p = np.ascontiguousarray(perm, np.int32)
+    T = np.zeros((H, W, D), np.float32)
+    lib().orc_target_box(_p(x, ctypes.c_float), H, W, D, _p(w, ctypes.c_float), int(normalize_),
+                         _p(p, ctypes.c_int32), phi, _p(T, ctypes.c_float))
+    return T
+
+
+def box_exp(x: np.ndarray, weights=None, normalize_: bool = True) -> int:
+    x = _f32(x)
+    n, D = x.shape
+    w = None if weights is None else _f32(weights)
+    return int(lib().orc_box_exp(_p(x, ctypes.c_float), n, D, _p(w, ctypes.c_float), int(normalize_)))
 
 
 def gather(src: np.ndarray, perm) -> np.ndarray:

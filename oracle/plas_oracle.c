@@ -154,7 +154,7 @@ typedef struct {
     int min_block;      /* 16 (Sec. 3.1)                                      */
     int shuffle_init;   /* 1: random initial placement (Sec. 3.1)             */
     int normalize;      /* 1: per-channel [0,1] normalisation (Sec. 3.1)      */
-    int pad_;
+    int target_mode;    /* 0: Gaussian target (Sec. 3.1); 1: box target      */
     long long max_iters;/* stop after this many iterations in total; 0 = none */
 } orc_schedule;
 
@@ -445,6 +445,7 @@ long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t
         memset(&s, 0, sizeof(s));
     }
     s.scale_exp = orc_scale_exp(x, N, D, w, sch->normalize);
+    const int box_exp = sch->target_mode == 1 ? orc_box_exp(x, N, D, w, sch->normalize) : 0;
     const double denom = ldexp((double)N, s.scale_exp);
     if (s.level >= nlev) s.done = 1;
 
@@ -461,7 +462,10 @@ long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t
         const int beta = orc_block_side(r, sch->min_block, H, W);
 
         /* (1) idealised target: low-pass filter of the current grid */
-        orc_blur(G, gs, H, W, D, r, sigma, T);
+        if (sch->target_mode == 1)
+            orc_box_target(G, gs, H, W, D, r, box_exp, T);
+        else
+            orc_blur(G, gs, H, W, D, r, sigma, T);
 
         /* (2) blocks shifted by a random (dy, dx) */
         int dy, dx;
@@ -549,6 +553,88 @@ long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t
     free(G);
     free(F);
     return ran;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Box target (a fast low-pass variant of the target, Sec. 3.1 asks only for */
+/* a low-pass filter whose radius shrinks): the mean of the in-range cells   */
+/* of the (2r+1) x (2r+1) window, on features in fixed point.                */
+/*   q = rint(F * 2^s) (int64), S = sum of q over the in-range window,       */
+/*   n = in-range cells, T = ((float)S / (float)n) * 2^-s   (FP32)           */
+/* s = the largest value <= 40 with B * 2^s <= 2^31, B = max_d |w_d| (times  */
+/* max(|lo_d|, |hi_d|) without normalisation) bounding every |F|.  The sums  */
+/* are exact integers, so the order of summation is free; here they are      */
+/* sliding window sums along y, then along x.                                */
+/* ------------------------------------------------------------------------- */
+int orc_box_exp(const float* x, long N, int D, const float* w, int normalize)
+{
+    double B = 0.0;
+    float* lo = (float*)malloc(sizeof(float) * (size_t)(D > 0 ? D : 1));
+    float* hi = (float*)malloc(sizeof(float) * (size_t)(D > 0 ? D : 1));
+    if (N > 0) orc_minmax(x, N, D, lo, hi);
+    for (int d = 0; d < D; ++d) {
+        double m = fabs((double)(w ? w[d] : 1.0f));
+        if (!normalize) m *= fmax(fabs((double)lo[d]), fabs((double)hi[d]));
+        if (m > B) B = m;
+    }
+    free(lo);
+    free(hi);
+    int s = 40;
+    while (s > -60 && ldexp(B, s) > 0x1p31) --s;
+    return s;
+}
+
+void orc_box_target(const float* G, int gs, int H, int W, int D, int r, int s_exp, float* T)
+{
+    const long N = (long)H * W;
+    long long* q = (long long*)malloc(sizeof(long long) * (size_t)N * D);
+    long long* sy = (long long*)malloc(sizeof(long long) * (size_t)N * D);
+    for (long p = 0; p < N; ++p)
+        for (int d = 0; d < D; ++d) q[p * D + d] = llrint(ldexp((double)G[p * gs + d], s_exp));
+    /* window sums along y: rows [y - r, y + r] within the grid */
+#pragma omp parallel for schedule(static)
+    for (long xd = 0; xd < (long)W * D; ++xd) {
+        const int x = (int)(xd / D), d = (int)(xd % D);
+        long long run = 0;
+        for (int y = 0; y <= r && y < H; ++y) run += q[((long)y * W + x) * D + d];
+        for (int y = 0; y < H; ++y) {
+            sy[((long)y * W + x) * D + d] = run;
+            if (y + r + 1 < H) run += q[((long)(y + r + 1) * W + x) * D + d];
+            if (y - r >= 0) run -= q[((long)(y - r) * W + x) * D + d];
+        }
+    }
+    /* window sums of those along x, then the mean over the in-range cells */
+#pragma omp parallel for schedule(static)
+    for (long yd = 0; yd < (long)H * D; ++yd) {
+        const int y = (int)(yd / D), d = (int)(yd % D);
+        const int ny = (y + r < H - 1 ? y + r : H - 1) - (y - r > 0 ? y - r : 0) + 1;
+        long long run = 0;
+        for (int x = 0; x <= r && x < W; ++x) run += sy[((long)y * W + x) * D + d];
+        for (int x = 0; x < W; ++x) {
+            const int nx = (x + r < W - 1 ? x + r : W - 1) - (x - r > 0 ? x - r : 0) + 1;
+            const float mean = (float)run / (float)(ny * nx);
+            T[((long)y * W + x) * D + d] = ldexpf(mean, -s_exp);
+            if (x + r + 1 < W) run += sy[((long)y * W + x + r + 1) * D + d];
+            if (x - r >= 0) run -= sy[((long)y * W + x - r) * D + d];
+        }
+    }
+    free(sy);
+    free(q);
+}
+
+/* Box target of a given arrangement at a given radius (per-step checks). */
+void orc_target_box(const float* x, int H, int W, int D, const float* w, int normalize,
+                    const int32_t* perm, double phi, float* T)
+{
+    const long N = (long)H * W;
+    float* F = (float*)malloc(sizeof(float) * (size_t)N * D);
+    float* G = (float*)malloc(sizeof(float) * (size_t)N * D);
+    orc_normalize(x, N, D, w, normalize, F);
+    for (long p = 0; p < N; ++p)
+        for (int d = 0; d < D; ++d) G[p * D + d] = F[(long)perm[p] * D + d];
+    orc_box_target(G, D, H, W, D, (int)floor(phi), orc_box_exp(x, N, D, w, normalize), T);
+    free(G);
+    free(F);
 }
 
 /* Target of a given arrangement at a given level (for per-step checks). */
