@@ -281,7 +281,8 @@ def run_plas(args):
     x_np, car_np = make_inputs(wl, seed=seed)
     x = torch.from_numpy(x_np).to(dev)
     car = torch.from_numpy(car_np).to(dev) if car_np is not None else None
-    ws = torch.empty(plas.sort_workspace_bytes(side, side, D), dtype=torch.uint8, device=dev)
+    ws = torch.empty(plas.sort_workspace_bytes(side, side, D, plas.Schedule(
+        target_mode=1 if args.target == "box" else 0)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     # launch shapes for this grid shape (the results do not depend on them):
@@ -297,9 +298,11 @@ def run_plas(args):
         tune = plas.get_tuning(side, side, D)
     t_tune = time.perf_counter() - t_tune
 
+    tmode = 1 if args.target == "box" else 0
+
     def step(profile):
         return plas.sort(x, side, side, carried=car, seed=seed, workspace=ws,
-                         schedule=plas.Schedule(profile=profile), want_stats=True)
+                         schedule=plas.Schedule(profile=profile, target_mode=tmode), want_stats=True)
 
     for _ in range(args.warmup):
         step(False)
@@ -347,7 +350,8 @@ def run_plas(args):
         xd.copy_(xh, non_blocking=True)
         if cd is not None:
             cd.copy_(ch, non_blocking=True)
-        r = plas.sort(xd, side, side, carried=cd, seed=seed, workspace=ws)
+        r = plas.sort(xd, side, side, carried=cd, seed=seed, workspace=ws,
+                      schedule=plas.Schedule(target_mode=tmode))
         ph.copy_(r.perm, non_blocking=True)
         if coh is not None:
             coh.copy_(r.carried, non_blocking=True)
@@ -373,6 +377,8 @@ def run_plas(args):
         "data": "synthetic (seeded numpy; 3DGS-shaped attributes, no dataset)",
         "config": {"workload": wl["desc"], "grid": f"{side}x{side}", "N": side * side, "D": D,
                    "carried": C, "iterations_per_sort": st0["iterations"], "levels": st0["levels"],
+                   "target": "box (fixed-point window mean, schedule.target_mode=1)" if tmode
+                             else "gaussian (default)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush",
                    "tuning": {"fir_small_below": tune["fir_small_below"],
@@ -599,7 +605,8 @@ def run_ncu_case(args):
     x_np, _ = make_inputs(wl, seed=0)
     x = torch.from_numpy(x_np).cuda()
     r = plas.sort(x, side, side, seed=0,
-                  schedule=plas.Schedule(max_iters=args.ncu_case, phi0=args.phi0),
+                  schedule=plas.Schedule(max_iters=args.ncu_case, phi0=args.phi0,
+                                         target_mode=1 if args.target == "box" else 0),
                   trace_cap=(1 << 20) if args.trace_out else 0)
     torch.cuda.synchronize()
     if args.trace_out:
@@ -616,6 +623,8 @@ def main():
     ap.add_argument("--impl", default="plas", choices=["plas", "reference"])
     ap.add_argument("--workload", default="m1", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--target", default="gaussian", choices=["gaussian", "box"],
+                    help="low-pass target of the sort: the Gaussian (default) or the box variant")
     ap.add_argument("--tune", default="auto", help="'auto' (run the autotuner) or "
                     "SMALL_BELOW,CTAS_PER_SM to pin the launch shapes")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",

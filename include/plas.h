@@ -74,6 +74,14 @@ typedef struct plas_schedule {
                         /* kernels read the level from device state, so one  */
                         /* graph serves every level); 0: direct launches.    */
                         /* Identical results either way.                     */
+    int target_mode;    /* 0: Gaussian target (Sec. 3.1, the default).       */
+                        /* 1: box target, a fast low-pass variant: the mean  */
+                        /* of the in-range cells of the (2r+1)^2 window on   */
+                        /* fixed-point features q = rint(F 2^s), s the       */
+                        /* largest <= 40 with max|F| bound * 2^s <= 2^31;    */
+                        /* T = ((float)S / (float)n) * 2^-s.  Its cost does  */
+                        /* not grow with r (summed-area tables).  Single     */
+                        /* sorts only (plas_sort, plas_target_box).          */
     long long* trace_S; /* device or NULL: trace_S[it] = fixed-point residual */
                         /* sum of iteration it (mean L2 distance * N * 2^k)  */
     int* trace_level;   /* device or NULL: level of iteration it             */
@@ -142,6 +150,9 @@ int plas_num_levels(int H, int W, const plas_schedule* sched /* host or NULL */)
 /* Device workspace plas_sort needs for an H x W grid of D sort channels
  * (C carried channels do not need workspace).  0 on invalid sizes. */
 size_t plas_sort_workspace_bytes(int H, int W, int D);
+/* The same for a given schedule (the box target needs an extra N x D int64
+ * table).  sched: host or NULL (defaults). */
+size_t plas_sort_workspace_bytes_ex(int H, int W, int D, const plas_schedule* sched);
 
 /*
  * plas_sort -- the PLAS grid sort (Sec. 3.1 and its "Blockwise Linear
@@ -224,6 +235,12 @@ int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float*
  */
 int plas_target(const float* x, int H, int W, int D, const float* weights, int normalize,
                 const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream);
+/* plas_target_box -- the box target of schedule.target_mode = 1 for one
+ * arrangement (the mean of the in-range cells of the (2r+1)^2 window,
+ * r = floor(phi), on fixed-point features; see plas_schedule).  Arguments as
+ * plas_target. */
+int plas_target_box(const float* x, int H, int W, int D, const float* weights, int normalize,
+                    const int32_t* perm, double phi, float* T, void* stream);
 
 /*
  * plas_group_permutation -- the grouping permutation of Sec. 3.1 ("a random

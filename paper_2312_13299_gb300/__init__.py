@@ -45,6 +45,7 @@ class Schedule:
     max_iters: int = 0
     profile: bool = False
     graphs: bool = True
+    target_mode: int = 0  # 0 Gaussian target, 1 box target (fast low-pass variant)
 
     def to_c(self, trace_S: Optional[torch.Tensor] = None,
              trace_level: Optional[torch.Tensor] = None) -> _lib.plas_schedule:
@@ -54,6 +55,7 @@ class Schedule:
         s.shuffle_init, s.normalize = int(self.shuffle_init), int(self.normalize)
         s.iters_per_poll, s.max_iters, s.profile = self.iters_per_poll, self.max_iters, int(self.profile)
         s.graphs = int(self.graphs)
+        s.target_mode = int(self.target_mode)
         s.trace_S = trace_S.data_ptr() if trace_S is not None else None
         s.trace_level = trace_level.data_ptr() if trace_level is not None else None
         cap = 0
@@ -126,8 +128,11 @@ def num_levels(H: int, W: int, schedule: Optional[Schedule] = None) -> int:
     return n
 
 
-def sort_workspace_bytes(H: int, W: int, D: int) -> int:
-    return int(load().plas_sort_workspace_bytes(H, W, D))
+def sort_workspace_bytes(H: int, W: int, D: int, schedule: Optional[Schedule] = None) -> int:
+    if schedule is None:
+        return int(load().plas_sort_workspace_bytes(H, W, D))
+    s = schedule.to_c()
+    return int(load().plas_sort_workspace_bytes_ex(H, W, D, ctypes.byref(s)))
 
 
 def sort(x: torch.Tensor, H: int, W: int, weights=None, carried: Optional[torch.Tensor] = None,
@@ -407,6 +412,20 @@ def target(x: torch.Tensor, H: int, W: int, perm: torch.Tensor, phi: float, weig
                                 perm.data_ptr(), float(phi), float(sigma_ratio), T.data_ptr(),
                                 _stream(x.device))
     check(rc, "plas_target")
+    return T
+
+
+def target_box(x: torch.Tensor, H: int, W: int, perm: torch.Tensor, phi: float, weights=None,
+               normalize: bool = True) -> torch.Tensor:
+    """Box target (schedule.target_mode = 1) of one arrangement -> [H, W, D]."""
+    x = _need_cuda(x, "x")
+    perm = _need_cuda(perm, "perm", torch.int32)
+    N, D = x.shape
+    T = torch.empty((H, W, D), dtype=torch.float32, device=x.device)
+    with torch.cuda.device(x.device):
+        rc = load().plas_target_box(x.data_ptr(), H, W, D, _weights(weights, D), int(normalize),
+                                    perm.data_ptr(), float(phi), T.data_ptr(), _stream(x.device))
+    check(rc, "plas_target_box")
     return T
 
 

@@ -32,7 +32,7 @@ class plas_schedule(ctypes.Structure):
     _fields_ = [("phi0", c_double), ("shrink", c_double), ("phi_min", c_double),
                 ("tol", c_double), ("sigma_ratio", c_double), ("min_block", c_int),
                 ("shuffle_init", c_int), ("normalize", c_int), ("iters_per_poll", c_int),
-                ("max_iters", c_ll), ("profile", c_int), ("graphs", c_int),
+                ("max_iters", c_ll), ("profile", c_int), ("graphs", c_int), ("target_mode", c_int),
                 ("trace_S", c_void_p), ("trace_level", c_void_p), ("trace_cap", c_ll)]
 
 
@@ -82,6 +82,7 @@ SIGNATURES = {
     "plas_default_schedule": (c_int, [P(plas_schedule)]),
     "plas_num_levels": (c_int, [c_int, c_int, P(plas_schedule)]),
     "plas_sort_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
+    "plas_sort_workspace_bytes_ex": (c_size_t, [c_int, c_int, c_int, P(plas_schedule)]),
     "plas_sort": (c_int, [c_void_p, c_int, c_int, c_int, P(c_float), c_void_p, c_int, c_uint64,
                           P(plas_schedule), c_void_p, P(plas_state), c_void_p, c_void_p,
                           c_void_p, c_void_p, c_size_t, P(plas_stats), c_void_p]),
@@ -89,6 +90,8 @@ SIGNATURES = {
     "plas_gather_rows": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "plas_target": (c_int, [c_void_p, c_int, c_int, c_int, P(c_float), c_int, c_void_p,
                             c_double, c_double, c_void_p, c_void_p]),
+    "plas_target_box": (c_int, [c_void_p, c_int, c_int, c_int, P(c_float), c_int, c_void_p,
+                                c_double, c_void_p, c_void_p]),
     "plas_group_permutation": (c_int, [c_uint64, c_uint32, c_uint64, c_uint32, c_void_p,
                                        c_void_p]),
     "plas_philox": (c_int, [c_void_p, c_uint32, c_uint32, c_int, c_void_p, c_void_p]),

@@ -1,0 +1,247 @@
+// box_kernels.cu -- the box target (schedule.target_mode = 1), a fast
+// low-pass variant of the idealised target of Sec. 3.1 (Morgenstern et al.,
+// arXiv 2312.13299): the mean of the in-range cells of the (2r+1) x (2r+1)
+// window around each cell, on fixed-point features q = rint(F 2^s).
+//
+// The window sums are exact int64 arithmetic, so they come from a summed-area
+// table I(y, x) = sum_{y' <= y, x' <= x} q: a scan along x per (row,
+// channel), a scan along y per (column, channel), then four corner reads
+// per output.  The cost does not depend on r.  Each output is
+//   T = ((float)S / (float)n) * 2^-s   (FP32, IEEE division),
+// the same bits as the oracle's sliding window sums.  The evaluation launch
+// also writes the iteration's grouping table.
+#include <algorithm>
+
+#include "plas_kernels.h"
+
+namespace plas {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kEvalThreads = 256;
+
+__device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }  // exact for |e| <= 126
+
+// The summed-area table holds DP = D rounded up to even int64 channels per
+// cell (the pad channel stays 0), so every channel pair is one aligned
+// 16-byte access.
+__host__ __device__ constexpr int sat_channels(int D) { return (D + 1) & ~1; }
+
+__device__ __forceinline__ long long shfl_up64(long long v, int delta) {
+    return (long long)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)v, delta);
+}
+
+// prefix sums along x of q = rint(F 2^s): one CTA per row; thread t owns the
+// cells [t*cpt, (t+1)*cpt) and all D channels (float4 loads of the cell's
+// features, 16-byte stores of channel pairs).  The per-thread channel totals
+// are scanned across the CTA with warp shuffles.  Exact int64.
+template <int D>
+__global__ void __launch_bounds__(kScanThreads) box_rowscan_kernel(const GridRef* __restrict__ grids) {
+    constexpr int GS = (D + 1 + 3) & ~3, DP = sat_channels(D);
+    __shared__ long long wtot[kScanThreads / 32][DP];
+    const GridRef& gr = grids[0];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const int W = gr.W, y = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int cpt = (W + kScanThreads - 1) / kScanThreads;
+    const int c0 = min(t * cpt, W), c1 = min(c0 + cpt, W);
+    const float scale = pow2f(st->box_exp);
+    const float* g = gr.G + (long long)y * W * GS;
+    auto load_q = [&](int x, long long* q) {
+        const float4* c = reinterpret_cast<const float4*>(g + (long long)x * GS);
+#pragma unroll
+        for (int k = 0; k < GS / 4; ++k) {
+            const float4 v = c[k];
+            const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * k + j < D) q[4 * k + j] = __float2ll_rn(__fmul_rn(f[j], scale));
+        }
+    };
+    long long tot[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) tot[d] = 0;
+    for (int x = c0; x < c1; ++x) {
+        long long q[D];
+        load_q(x, q);
+#pragma unroll
+        for (int d = 0; d < D; ++d) tot[d] += q[d];
+    }
+    // exclusive prefix of the thread totals, per channel, across the CTA
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        long long v = tot[d];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = shfl_up64(v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wtot[warp][d] = v;
+        tot[d] = v - tot[d];  // exclusive within the warp
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        long long off = 0;
+        for (int w = 0; w < warp; ++w) off += wtot[w][d];
+        tot[d] += off;
+    }
+    long long* out = gr.sat + (long long)y * W * DP;
+    for (int x = c0; x < c1; ++x) {
+        long long q[D];
+        load_q(x, q);
+#pragma unroll
+        for (int d = 0; d < D; ++d) tot[d] += q[d];
+        longlong2* o = reinterpret_cast<longlong2*>(out + (long long)x * DP);
+#pragma unroll
+        for (int k = 0; k < DP / 2; ++k)
+            o[k] = make_longlong2(tot[2 * k], 2 * k + 1 < D ? tot[2 * k + 1] : 0LL);
+    }
+}
+
+// prefix sums along y of the row sums, in place: one CTA per cell column;
+// thread (k, j) owns row segment k of channel pair j (16-byte accesses).
+// Phase 1 sums the segments, phase 2 scans the segment totals per pair,
+// phase 3 walks the segments again (L1-resident: one cell column is
+// H x DP x 8 bytes) and writes the prefix sums.
+__global__ void __launch_bounds__(kScanThreads) box_colscan_kernel(const GridRef* __restrict__ grids, int DP) {
+    __shared__ longlong2 tot[kScanThreads];
+    const GridRef& gr = grids[0];
+    if (sweep_idle(gr.st)) return;
+    const int H = gr.H, W = gr.W, x = blockIdx.x;
+    const int pairs = DP / 2;
+    const int K = kScanThreads / pairs;
+    const int L = (H + K - 1) / K;
+    const int t = threadIdx.x, k = t / pairs, j = t - (t / pairs) * pairs;
+    const bool act = k < K;
+    const int y0 = min(k * L, H), y1 = min(y0 + L, H);
+    const long long row = (long long)W * DP / 2;  // longlong2 per row
+    longlong2* p = reinterpret_cast<longlong2*>(gr.sat) + (long long)x * pairs + j;
+    long long s0 = 0, s1 = 0;
+    if (act) {
+        int y = y0;
+        for (; y + 4 <= y1; y += 4) {
+            const longlong2 a = p[(long long)y * row], b = p[(long long)(y + 1) * row];
+            const longlong2 c = p[(long long)(y + 2) * row], e = p[(long long)(y + 3) * row];
+            s0 += a.x + b.x + c.x + e.x;
+            s1 += a.y + b.y + c.y + e.y;
+        }
+        for (; y < y1; ++y) {
+            const longlong2 a = p[(long long)y * row];
+            s0 += a.x;
+            s1 += a.y;
+        }
+    }
+    tot[t] = make_longlong2(s0, s1);
+    __syncthreads();
+    if (t < pairs) {
+        long long r0 = 0, r1 = 0;
+        for (int kk = 0; kk < K; ++kk) {
+            const longlong2 v = tot[kk * pairs + t];
+            tot[kk * pairs + t] = make_longlong2(r0, r1);
+            r0 += v.x;
+            r1 += v.y;
+        }
+    }
+    __syncthreads();
+    if (act) {
+        long long r0 = tot[t].x, r1 = tot[t].y;
+        for (int y = y0; y < y1; ++y) {
+            const longlong2 a = p[(long long)y * row];
+            r0 += a.x;
+            r1 += a.y;
+            p[(long long)y * row] = make_longlong2(r0, r1);
+        }
+    }
+}
+
+// window mean from four corners of the summed-area table, a channel pair per
+// thread; writes T and the grouping table
+__global__ void __launch_bounds__(kEvalThreads) box_eval_kernel(const GridRef* __restrict__ grids, int D,
+                                                                int ts) {
+    const GridRef& gr = grids[0];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const LevelDesc& lv = gr.lv[st->level];
+    const int H = gr.H, W = gr.W, r = lv.r;
+    const int DP = sat_channels(D), pairs = DP / 2;
+    const float inv_scale = pow2f(-st->box_exp);
+    const long long total = (long long)H * W * pairs;
+    const long long rowp = (long long)W * pairs;
+    const longlong2* I = reinterpret_cast<const longlong2*>(gr.sat);
+    for (long long e = (long long)blockIdx.x * kEvalThreads + threadIdx.x; e < total;
+         e += (long long)gridDim.x * kEvalThreads) {
+        const long long cell = e / pairs;
+        const int j = (int)(e - cell * pairs);
+        const int y = (int)(cell / W), x = (int)(cell - (long long)y * W);
+        const int y0 = max(y - r, 0) - 1, y1 = min(y + r, H - 1);
+        const int x0 = max(x - r, 0) - 1, x1 = min(x + r, W - 1);
+        longlong2 S = I[(long long)y1 * rowp + (long long)x1 * pairs + j];
+        if (y0 >= 0) {
+            const longlong2 v = I[(long long)y0 * rowp + (long long)x1 * pairs + j];
+            S.x -= v.x;
+            S.y -= v.y;
+        }
+        if (x0 >= 0) {
+            const longlong2 v = I[(long long)y1 * rowp + (long long)x0 * pairs + j];
+            S.x -= v.x;
+            S.y -= v.y;
+        }
+        if (y0 >= 0 && x0 >= 0) {
+            const longlong2 v = I[(long long)y0 * rowp + (long long)x0 * pairs + j];
+            S.x += v.x;
+            S.y += v.y;
+        }
+        const float n = (float)((y1 - y0) * (x1 - x0));
+        float* o = gr.T + cell * ts + 2 * j;
+        o[0] = __fmul_rn(__fdiv_rn(__ll2float_rn(S.x), n), inv_scale);
+        if (2 * j + 1 < D) o[1] = __fmul_rn(__fdiv_rn(__ll2float_rn(S.y), n), inv_scale);
+    }
+    write_group_table(gr, lv, st, blockIdx.x, gridDim.x, kEvalThreads);
+}
+
+template <int D>
+void launch_rowscan_t(const GridRef* grid, int H, cudaStream_t s) {
+    box_rowscan_kernel<D><<<(unsigned)H, kScanThreads, 0, s>>>(grid);
+}
+
+void launch_rowscan(const GridRef* grid, int H, int D, cudaStream_t s) {
+    switch (D) {
+        case 1: launch_rowscan_t<1>(grid, H, s); break;
+        case 2: launch_rowscan_t<2>(grid, H, s); break;
+        case 3: launch_rowscan_t<3>(grid, H, s); break;
+        case 4: launch_rowscan_t<4>(grid, H, s); break;
+        case 5: launch_rowscan_t<5>(grid, H, s); break;
+        case 6: launch_rowscan_t<6>(grid, H, s); break;
+        case 7: launch_rowscan_t<7>(grid, H, s); break;
+        case 8: launch_rowscan_t<8>(grid, H, s); break;
+        case 9: launch_rowscan_t<9>(grid, H, s); break;
+        case 10: launch_rowscan_t<10>(grid, H, s); break;
+        case 11: launch_rowscan_t<11>(grid, H, s); break;
+        case 12: launch_rowscan_t<12>(grid, H, s); break;
+        case 13: launch_rowscan_t<13>(grid, H, s); break;
+        case 14: launch_rowscan_t<14>(grid, H, s); break;
+        case 15: launch_rowscan_t<15>(grid, H, s); break;
+        case 16: launch_rowscan_t<16>(grid, H, s); break;
+        case 20: launch_rowscan_t<20>(grid, H, s); break;
+        case 24: launch_rowscan_t<24>(grid, H, s); break;
+        case 32: launch_rowscan_t<32>(grid, H, s); break;
+        case 48: launch_rowscan_t<48>(grid, H, s); break;
+        default: launch_rowscan_t<64>(grid, H, s); break;
+    }
+}
+
+}  // namespace
+
+void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cudaStream_t s) {
+    launch_rowscan(grid, H, D, s);                                          // one CTA per row
+    box_colscan_kernel<<<(unsigned)W, kScanThreads, 0, s>>>(grid, sat_channels(D));  // per cell column
+    const long long total = (long long)H * W * (sat_channels(D) / 2);
+    const unsigned blocks = (unsigned)std::min<long long>((total + kEvalThreads - 1) / kEvalThreads,
+                                                          (long long)num_sms * 8);
+    box_eval_kernel<<<blocks, kEvalThreads, 0, s>>>(grid, D, target_stride(D));
+}
+
+}  // namespace plas

@@ -130,7 +130,8 @@ class Engine {
         sl->N = (long long)H * W;
         sl->geo = build_geometry(s_, H, W);
         sl->nlev = (int)sl->geo.lv.size();
-        workspace_layout(H, W, D_, sl->nlev, sl->geo.table_floats, &sl->ws, sl->mem);
+        workspace_layout(H, W, D_, sl->nlev, sl->geo.table_floats, &sl->ws, sl->mem,
+                         s_.target_mode == 1);
         DevState init{};
         if (j.resume) {
             init.it = j.init.it;
@@ -150,6 +151,8 @@ class Engine {
         ref.st = sl->ws.st; ref.lv = sl->ws.lv; ref.table = sl->ws.table;
         ref.H = H; ref.W = W; ref.nlev = sl->nlev; ref.seed = j.seed;
         ref.trace_S = j.trace_S; ref.trace_level = j.trace_level; ref.trace_cap = j.trace_cap;
+        ref.target_mode = s_.target_mode;
+        ref.sat = sl->ws.sat;
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st_));
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.ref, &ref, sizeof(GridRef), cudaMemcpyHostToDevice, st_));
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.lv, sl->geo.lv.data(), sizeof(LevelDesc) * sl->nlev,
@@ -343,8 +346,15 @@ class Engine {
             for (int c = 0; c < kClsCount; ++c) {
                 cudaEvent_t e0 = events ? begin() : nullptr;
                 switch (c) {
-                    case kClsFirY: launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st); break;
-                    case kClsFirX: launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st); break;
+                    case kClsFirY:
+                        if (s_.target_mode == 1)  // box target (single grid): all of it here
+                            launch_box_target(p.grids, active_[0]->job.H, active_[0]->job.W, D_, nsm_, st);
+                        else
+                            launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st);
+                        break;
+                    case kClsFirX:
+                        if (s_.target_mode != 1) launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st);
+                        break;
                     default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st); break;
                 }
                 if (events) end(e0, c);
@@ -418,6 +428,8 @@ class Engine {
             r.nlev = sl->nlev; r.seed = sl->job.seed;
             r.trace_S = sl->job.trace_S; r.trace_level = sl->job.trace_level;
             r.trace_cap = sl->job.trace_cap;
+            r.target_mode = s_.target_mode;
+            r.sat = sl->ws.sat;
         }
         std::vector<CtaMap> maps;
         for (int c = 0; c < kClsCount; ++c) {
@@ -670,9 +682,11 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
                 for (int c = 0; c < PLAS_K_COUNT; ++c) stats->kernel[c] = eng.ks_[c];
                 const double its = (double)(fin.it - (resume ? state_io->it : 0));
                 stats->kernel[PLAS_K_PREP].bytes = (double)N * D * 8 + (double)N * grid_stride(D) * 4;
+                // target: read the features, write the target (8 N D bytes per
+                // iteration); the Gaussian takes two passes, each counted in full
                 stats->kernel[PLAS_K_BLUR_COLS].bytes = its * 8.0 * (double)N * D;
                 stats->kernel[PLAS_K_BLUR_COLS].flops = 2.0 * fin.fmas_y;
-                stats->kernel[PLAS_K_BLUR_ROWS].bytes = its * 8.0 * (double)N * D;
+                stats->kernel[PLAS_K_BLUR_ROWS].bytes = s.target_mode == 1 ? 0.0 : its * 8.0 * (double)N * D;
                 stats->kernel[PLAS_K_BLUR_ROWS].flops = 2.0 * fin.fmas_x;
                 // the grouping table is written by the pass-0 launches
                 stats->kernel[PLAS_K_BLUR_COLS].bytes += 4.0 * fin.beta2_sum;
@@ -875,6 +889,7 @@ extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* 
     s.trace_level = nullptr;
     s.trace_cap = 0;
     if (int e = validate_schedule(s)) return e;
+    if (s.target_mode != 0) return fail(PLAS_ERR_INVALID_ARG, "the box target is available for single sorts");
     Weights w{};
     if (int e = make_weights(weights, D, &w)) return e;
     for (int i = 0; i < n; ++i) {
@@ -1025,6 +1040,7 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
     srv->s.trace_level = nullptr;
     srv->s.trace_cap = 0;
     if (int e = validate_schedule(srv->s)) return e;
+    if (srv->s.target_mode != 0) return fail(PLAS_ERR_INVALID_ARG, "the box target is available for single sorts");
     srv->budget = mem_budget;
     srv->st = (cudaStream_t)stream;
     srv->eng = std::make_unique<Engine>(D, srv->w, srv->s, srv->st);

@@ -274,19 +274,9 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
         }
     }
 
-    if (pass == 0) {
-        // The grouping permutation of this iteration (Sec. 3.1, one random
-        // permutation of the beta^2 block cells shared by all blocks),
-        // pi[m] for m < beta^2, spread over this grid's CTAs of the pass; the
-        // assignment launch that follows reads it.  The state is not written
-        // before that launch's schedule step.
-        const uint32_t n = (uint32_t)lv.beta * (uint32_t)lv.beta;
-        const uint32_t h = feistel_half_bits(n);
-        const uint64_t it = (uint64_t)st->it;
-        const uint32_t stride = (uint32_t)cr.count * kFirThreads;
-        for (uint32_t m = (uint32_t)cr.local * kFirThreads + threadIdx.x; m < n; m += stride)
-            gr.pi[m] = keyed_permute(m, n, h, gr.seed, kTagGroup, it);
-    }
+    // the iteration's grouping table (the state is not written before the
+    // assignment launch's schedule step)
+    if (pass == 0) write_group_table(gr, lv, st, cr.local, cr.count, kFirThreads);
 }
 
 int fir_ctas(int rows, int cols, int variant) {

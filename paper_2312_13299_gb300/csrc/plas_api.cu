@@ -60,6 +60,7 @@ int validate_schedule(const plas_schedule& s) {
     if (s.max_iters < 0) return fail(PLAS_ERR_INVALID_ARG, "max_iters must be >= 0");
     if (s.trace_cap < 0) return fail(PLAS_ERR_INVALID_ARG, "trace_cap must be >= 0");
     if (!(s.phi0 <= 1e7)) return fail(PLAS_ERR_INVALID_ARG, "phi0 too large");
+    if (s.target_mode != 0 && s.target_mode != 1) return fail(PLAS_ERR_INVALID_ARG, "target_mode must be 0 or 1");
     return PLAS_OK;
 }
 
@@ -137,7 +138,7 @@ Geometry build_geometry(const plas_schedule& s, int H, int W) {
 // per-grid workspace
 // ---------------------------------------------------------------------------
 size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Workspace* ws,
-                        char* base) {
+                        char* base, bool sat) {
     const long long N = (long long)H * W;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -155,13 +156,15 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
     w.lv = (LevelDesc*)take(sizeof(LevelDesc) * (size_t)nlev);
     w.table = (float*)take(sizeof(float) * table_floats);
     w.macc = (double*)take(sizeof(double) * 4);
+    w.sat = sat ? (long long*)take(sizeof(long long) * (size_t)N * ((D + 1) & ~1)) : nullptr;
     if (ws) *ws = w;
     return off;
 }
 
 size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s) {
     Geometry g = build_geometry(s, H, W);
-    return workspace_layout(H, W, D, (int)g.lv.size(), g.table_floats, nullptr, nullptr);
+    return workspace_layout(H, W, D, (int)g.lv.size(), g.table_floats, nullptr, nullptr,
+                            s.target_mode == 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +334,14 @@ size_t plas_sort_workspace_bytes(int H, int W, int D) {
     return sort_workspace_bytes(H, W, D, s);
 }
 
+size_t plas_sort_workspace_bytes_ex(int H, int W, int D, const plas_schedule* sched) {
+    if (H < 1 || W < 1 || !channels_supported(D) || !grid_fits(H, W, D)) return 0;
+    plas_schedule s;
+    if (sched) s = *sched; else plas_default_schedule(&s);
+    if (validate_schedule(s) != PLAS_OK) return 0;
+    return sort_workspace_bytes(H, W, D, s);
+}
+
 int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float* dst, void* stream) {
     g_last_error.clear();
     if (N < 0 || C < 1) return fail(PLAS_ERR_INVALID_ARG, "N >= 0 and C >= 1 required");
@@ -350,8 +361,9 @@ int plas_select_rows(const float* src, long long n_src, int C, const int32_t* id
     return check_launch("select_rows");
 }
 
-int plas_target(const float* x, int H, int W, int D, const float* weights, int normalize,
-                const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream) {
+static int target_impl(const float* x, int H, int W, int D, const float* weights, int normalize,
+                       const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream,
+                       int mode) {
     g_last_error.clear();
     if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad sizes");
     if (!grid_fits(H, W, D)) return fail(PLAS_ERR_INVALID_ARG, "grid too large (H*W and max(H, W)*D must be <= 2^26)");
@@ -367,19 +379,21 @@ int plas_target(const float* x, int H, int W, int D, const float* weights, int n
     s.normalize = normalize;
     Geometry g = build_geometry(s, H, W);
     Workspace ws{};
-    const size_t need = workspace_layout(H, W, D, 1, g.table_floats, nullptr, nullptr);
+    const size_t need = workspace_layout(H, W, D, 1, g.table_floats, nullptr, nullptr, mode == 1);
     void* mem = nullptr;
     if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(PLAS_ERR_OOM, "workspace allocation failed");
     }
-    workspace_layout(H, W, D, 1, g.table_floats, &ws, (char*)mem);
+    workspace_layout(H, W, D, 1, g.table_floats, &ws, (char*)mem, mode == 1);
     Weights w{};
     for (int d = 0; d < D; ++d) w.w[d] = weights ? weights[d] : 1.0f;
     DevState init{};
     GridRef ref{};
     ref.G = ws.G; ref.T = ws.T; ref.H1 = ws.H1; ref.pi = ws.pi; ref.st = ws.st;
     ref.lv = ws.lv; ref.table = ws.table; ref.H = H; ref.W = W; ref.nlev = 1;
+    ref.target_mode = mode;
+    ref.sat = ws.sat;
     int rc = PLAS_OK;
     do {
         if (cudaMemcpyAsync(ws.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -395,9 +409,13 @@ int plas_target(const float* x, int H, int W, int D, const float* weights, int n
         launch_finalize_prep(ws.st, N, D, w, normalize, st);
         launch_pack(x, (int)N, D, w, normalize, ws.st, 2, perm, 0, ws.G, st);
         launch_norms(ws.lv, 1, H, W, ws.table, st);
-        const int var = g.lv[0].r < tuning_for(H, W, D).small_below ? kFirSmallRadius : kFirLargeRadius;
-        launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st);
-        launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st);
+        if (mode == 1) {
+            launch_box_target(ws.ref, H, W, D, num_sms(), st);
+        } else {
+            const int var = g.lv[0].r < tuning_for(H, W, D).small_below ? kFirSmallRadius : kFirLargeRadius;
+            launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st);
+            launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st);
+        }
         launch_copy_features(ws.T, (int)N, D, target_stride(D), T, st);
         rc = check_launch("target");
         if (rc != PLAS_OK) break;
@@ -412,6 +430,16 @@ int plas_target(const float* x, int H, int W, int D, const float* weights, int n
     } while (0);
     cudaFreeAsync(mem, st);
     return rc;
+}
+
+int plas_target(const float* x, int H, int W, int D, const float* weights, int normalize,
+                const int32_t* perm, double phi, double sigma_ratio, float* T, void* stream) {
+    return target_impl(x, H, W, D, weights, normalize, perm, phi, sigma_ratio, T, stream, 0);
+}
+
+int plas_target_box(const float* x, int H, int W, int D, const float* weights, int normalize,
+                    const int32_t* perm, double phi, float* T, void* stream) {
+    return target_impl(x, H, W, D, weights, normalize, perm, phi, 2.0, T, stream, 1);
 }
 
 int plas_group_permutation(uint64_t seed, uint32_t tag, uint64_t counter, uint32_t n,

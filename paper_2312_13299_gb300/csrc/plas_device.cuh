@@ -112,7 +112,7 @@ struct DevState {
     unsigned int arrivals;    // CTAs of the running assignment launch that finished
     int nonfinite;            // input held NaN / Inf
     int bad_index;            // a caller-supplied permutation entry was out of range
-    int pad_;
+    int box_exp;              // box target: fixed-point exponent s of the features
     long long grouped;        // cells that took part in a group, summed
     long long max_iters;      // 0 = none
     // work of the iterations run (for the algorithmic roofline counts)

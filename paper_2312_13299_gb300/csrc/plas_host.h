@@ -61,9 +61,10 @@ struct Workspace {
     LevelDesc* lv;
     float* table;
     double* macc;
+    long long* sat;  // box target: summed-area table, N x round_up(D, 2) int64 (else null)
 };
 size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Workspace* ws,
-                        char* base);
+                        char* base, bool sat = false);
 size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 
 // ---- launch-shape tuning (tune.cu) ---------------------------------------------------

@@ -51,11 +51,12 @@ struct GridRef {
     const float* table;   // level table (taps, norms)
     int H, W;
     int nlev;
-    int pad_;
+    int target_mode;      // 0 Gaussian target, 1 box target
     uint64_t seed;
     long long* trace_S;   // optional per-iteration residual sums
     int* trace_level;     // optional per-iteration level
     long long trace_cap;
+    long long* sat;       // box target: N x round_up(D, 2) int64 summed-area table
 };
 
 // CTA -> grid map entry of a batched launch.
@@ -76,6 +77,21 @@ __device__ __forceinline__ CtaRef resolve_cta(const CtaMap* __restrict__ map) {
     if (map == nullptr) return CtaRef{0, (int)blockIdx.x, (int)gridDim.x};
     const CtaMap m = map[blockIdx.x];
     return CtaRef{m.grid, m.local, m.count};
+}
+
+// The grouping permutation of the current iteration (Sec. 3.1: one random
+// permutation of the beta^2 block cells, shared by all blocks), pi[m] for
+// m < beta^2, spread over 'count' CTAs of 'threads' threads (this CTA is
+// number 'local').  The assignment launch that follows reads it.
+__device__ __forceinline__ void write_group_table(const GridRef& gr, const LevelDesc& lv,
+                                                  const DevState* st, int local, int count,
+                                                  int threads) {
+    const uint32_t n = (uint32_t)lv.beta * (uint32_t)lv.beta;
+    const uint32_t h = feistel_half_bits(n);
+    const uint64_t it = (uint64_t)st->it;
+    const uint32_t stride = (uint32_t)count * (uint32_t)threads;
+    for (uint32_t m = (uint32_t)local * (uint32_t)threads + threadIdx.x; m < n; m += stride)
+        gr.pi[m] = keyed_permute(m, n, h, gr.seed, kTagGroup, it);
 }
 
 // Cell strides of the working grid G (features + index, padded to float4) and
@@ -111,6 +127,9 @@ void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int
                 cudaStream_t s);
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
                    cudaStream_t s);
+
+// ---- box target (target_mode 1): one grid -------------------------------------
+void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cudaStream_t s);
 
 // ---- outputs -----------------------------------------------------------------
 void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream_t s);

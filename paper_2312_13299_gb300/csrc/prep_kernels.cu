@@ -99,6 +99,19 @@ __global__ void finalize_prep_kernel(DevState* st, long long N, int D, Weights w
     int k = 32;
     while (k > 0 && ldexp(m, k) >= 4611686018427387904.0 /* 2^62 */) --k;
     st->scale_exp = k;
+    // box target: fixed-point exponent s, the largest <= 40 with B 2^s <= 2^31
+    // for B = max_d |w_d| (times max(|lo_d|, |hi_d|) without normalisation)
+    double B = 0.0;
+    for (int d = 0; d < D; ++d) {
+        double b = fabs((double)w.w[d]);
+        if (!normalize && N > 0)
+            b = __dmul_rn(b, fmax(fabs((double)ordered_to_float(st->lo_bits[d])),
+                                  fabs((double)ordered_to_float(st->hi_bits[d]))));
+        B = fmax(B, b);
+    }
+    int s = 40;
+    while (s > -60 && ldexp(B, s) > 2147483648.0 /* 2^31 */) --s;
+    st->box_exp = s;
     if (st->nonfinite) {
         st->status = -5;  // PLAS_ERR_NONFINITE
         st->done = 1;

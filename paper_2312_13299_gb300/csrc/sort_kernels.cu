@@ -305,8 +305,9 @@ __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
         if (ticket == (unsigned)cr.count - 1u) {
             __threadfence();
             const LevelDesc& lv = gr.lv[st->level];
-            const double fy = pass_taps(H, lv.ry) * (double)W * D;
-            const double fx = pass_taps(W, lv.rx) * (double)H * D;
+            // in-range tap FMAs of the Gaussian passes (none for the box target)
+            const double fy = gr.target_mode == 1 ? 0.0 : pass_taps(H, lv.ry) * (double)W * D;
+            const double fx = gr.target_mode == 1 ? 0.0 : pass_taps(W, lv.rx) * (double)H * D;
             schedule_step(st, (long long)H * W, nby, nbx, ngroups, gr.nlev, tol, gr.trace_S, gr.trace_level,
                           gr.trace_cap, fy, fx, (double)beta * beta);
         }
