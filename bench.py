@@ -9,6 +9,7 @@ iteration of the shrinking-radius schedule, permutation + carried gather).
 
   python bench.py [--steps K] [--warmup W] [--workload m1|cfg2|cfg3|cfg1|p0]
   python bench.py --impl reference      # the CPU oracle on this host's cores
+  python bench.py --workload p0 --threshold-sweep   # VAD vs runtime over tol
 
 Under torchrun (N > 1) every rank sorts its own replica (different seed): the
 sort has no data-path exchange, so the job is N independent replicas and
@@ -286,15 +287,16 @@ def run_plas(args):
     stream = torch.cuda.current_stream(dev)
 
     # launch shapes for this grid shape (the results do not depend on them):
-    # measured by the autotuner, or pinned with --tune SMALL_BELOW,CTAS_PER_SM
+    # measured by the autotuner, or pinned with --tune SMALL_BELOW,MEDIUM_BELOW,CTAS_PER_SM
     # (a profiler distorts the tuner's own timings, so profiled runs pin the
     # values a plain run chose)
     t_tune = time.perf_counter()
     if args.tune == "auto":
         tune = plas.autotune(side, side, D)
     else:
-        sb, per = (int(v) for v in args.tune.split(","))
-        plas.set_tuning(side, side, D, fir_small_below=sb, assign_ctas_per_sm=per)
+        sb, mb, per = (int(v) for v in args.tune.split(","))
+        plas.set_tuning(side, side, D, fir_small_below=sb, fir_medium_below=mb,
+                        assign_ctas_per_sm=per)
         tune = plas.get_tuning(side, side, D)
     t_tune = time.perf_counter() - t_tune
 
@@ -382,6 +384,7 @@ def run_plas(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2_policy": "working set (grid, target, row pass, inputs, carried) > 129 MB L2; no flush",
                    "tuning": {"fir_small_below": tune["fir_small_below"],
+                              "fir_medium_below": tune["fir_medium_below"],
                               "assign_ctas_per_sm": tune["assign_ctas_per_sm"],
                               "source": "autotune" if args.tune == "auto" else "pinned",
                               "autotune_s": round(t_tune, 2)}},
@@ -594,6 +597,51 @@ def run_loss(args):
     print(json.dumps(line), flush=True)
 
 
+def run_threshold_sweep(args):
+    """Sorting quality against runtime over the stall threshold (the
+    break-threshold study of the supplementary), for the Gaussian and the box
+    target: per (target, tol) and input seed (3 seeds), one warm-up sort and
+    one CUDA-event-timed sort of the workload (default: 512 x 512 x 3
+    U[0,1)) with autotuned launch shapes; reported are the means over the
+    seeds of the time, the iterations and the VAD of the sorted grid on
+    values x 255."""
+    import torch
+    import paper_2312_13299_gb300 as plas
+    plas.load()
+    wl = WORKLOADS[args.workload]
+    side = wl["side"]
+    plas.autotune(side, side, wl["D"])
+    seeds = (0, 1, 2)
+    xs = [torch.from_numpy(make_inputs(wl, seed=s)[0]).cuda() for s in seeds]
+    tols = [float(t) for t in args.tols.split(",")]
+    results = []
+    for target in ("gaussian", "box"):
+        for tol in tols:
+            sch = plas.Schedule(tol=tol, target_mode=1 if target == "box" else 0)
+            ms, its, vads = [], [], []
+            for s, x in zip(seeds, xs):
+                plas.sort(x, side, side, seed=s, schedule=sch)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                r = plas.sort(x, side, side, seed=s, schedule=sch, want_sorted=True)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                its.append(int(r.state["it"]))
+                vads.append(plas.grid_metrics(r.sorted.view(side, side, wl["D"]), scale=255.0)[1])
+            results.append({"target": target, "tol": tol, "ms": round(statistics.mean(ms), 2),
+                            "iterations": round(statistics.mean(its), 1),
+                            "vad": round(statistics.mean(vads), 3),
+                            "vad_per_seed": [round(v, 3) for v in vads]})
+    vad0 = statistics.mean(plas.grid_metrics(x.view(side, side, wl["D"]), scale=255.0)[1]
+                           for x in xs)
+    line = {"metric": "VAD and ms per sort over the stall threshold", "workload": wl["desc"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic", "vad_unsorted": round(vad0, 2), "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(args):
     """A bounded launch sequence for profiler captures: the workload's inputs,
     one sort capped at --ncu-case iterations (all at the top radius levels)."""
@@ -626,7 +674,7 @@ def main():
     ap.add_argument("--target", default="gaussian", choices=["gaussian", "box"],
                     help="low-pass target of the sort: the Gaussian (default) or the box variant")
     ap.add_argument("--tune", default="auto", help="'auto' (run the autotuner) or "
-                    "SMALL_BELOW,CTAS_PER_SM to pin the launch shapes")
+                    "SMALL_BELOW,MEDIUM_BELOW,CTAS_PER_SM to pin the launch shapes")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="run one sort of the workload capped at ITERS iterations and exit "
                          "(a small, bounded program for ncu captures; prints nothing)")
@@ -638,6 +686,11 @@ def main():
                     help="served-stream benchmark (continuous batching vs plain), own JSON line")
     ap.add_argument("--loss", action="store_true",
                     help="smoothness-loss fwd/bwd benchmark on 1024x1024x59, own JSON line")
+    ap.add_argument("--threshold-sweep", action="store_true",
+                    help="VAD and runtime over the stall threshold, Gaussian and box target, "
+                         "own JSON line (use with --workload p0)")
+    ap.add_argument("--tols", default="1e-2,3e-3,1e-3,3e-4,1e-4,3e-5,1e-5",
+                    help="with --threshold-sweep: the thresholds")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
     ap.add_argument("--policies", default="fifo_fill,shortest_first,all",
@@ -652,6 +705,9 @@ def main():
         return
     if args.loss:
         run_loss(args)
+        return
+    if args.threshold_sweep:
+        run_threshold_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

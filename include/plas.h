@@ -431,13 +431,14 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
 /* ---------------------------------------------------------------------- */
 /*
  * Launch shapes the sort can choose without changing any result: the FIR
- * tiling of the target passes (a 128-row tiling with 16 warps per CTA, or a
- * 32-row tiling with 4 CTAs per SM; the same FMA chains either way) and the
+ * tiling of the target passes (128 rows per CTA with 16 warps, 64 rows with
+ * 2 CTAs per SM, or 32 rows with 4 CTAs per SM; the same FMA chains in every
+ * case) and the
  * number of assignment CTAs (the residual sum is exact and order-free).  The
  * paper has no counterpart; it is GPU plumbing.
  *
  * plas_autotune: times the candidates on a synthetic H x W x D grid (seeded
- *   uniform values made on the device): both FIR tilings at radii from 1 up
+ *   uniform values made on the device): the three FIR tilings at radii from 1 up
  *   to the grid's start radius, and the assignment at 2, 4, 8 and 16 CTAs
  *   per SM at the start radius and at radius 8.  It installs the fastest
  *   choice for sorts on this device with D channels and the nearest cell
@@ -446,18 +447,22 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   PLAS_ERR_INVALID_ARG for unsupported sizes.
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
- *   shape on the current device would use (the defaults 24 and 8 when
- *   nothing is installed).  Thread-safe.
+ *   shape on the current device would use (the defaults 1, 96 and 8 when
+ *   nothing is installed).  A radius r takes the 32-row tiling when
+ *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
+ *   the 128-row one.  Thread-safe.
  */
 #define PLAS_TUNE_MAX_RADII 16
 #define PLAS_TUNE_ASSIGN_CANDIDATES 4
 typedef struct plas_tuning {
     int fir_small_below;    /* the 32-row FIR tiling for radii below this      */
+    int fir_medium_below;   /* else the 64-row tiling for radii below this     */
     int assign_ctas_per_sm; /* cap on assignment CTAs per SM, 1..16           */
     int n_radii;            /* radii measured by plas_autotune                */
     int radius[PLAS_TUNE_MAX_RADII];
-    float fir_small_us[PLAS_TUNE_MAX_RADII]; /* both passes, 32-row tiling    */
-    float fir_large_us[PLAS_TUNE_MAX_RADII]; /* both passes, 128-row tiling   */
+    float fir_small_us[PLAS_TUNE_MAX_RADII];  /* both passes, 32-row tiling   */
+    float fir_medium_us[PLAS_TUNE_MAX_RADII]; /* both passes, 64-row tiling   */
+    float fir_large_us[PLAS_TUNE_MAX_RADII];  /* both passes, 128-row tiling  */
     int assign_per_sm[PLAS_TUNE_ASSIGN_CANDIDATES];
     float assign_us[PLAS_TUNE_ASSIGN_CANDIDATES]; /* sum over the two radii   */
 } plas_tuning;

@@ -243,8 +243,10 @@ def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] 
 
 def _tuning_dict(t: "_lib.plas_tuning") -> dict:
     n = t.n_radii
-    return {"fir_small_below": t.fir_small_below, "assign_ctas_per_sm": t.assign_ctas_per_sm,
+    return {"fir_small_below": t.fir_small_below, "fir_medium_below": t.fir_medium_below,
+            "assign_ctas_per_sm": t.assign_ctas_per_sm,
             "radius": list(t.radius[:n]), "fir_small_us": [round(v, 2) for v in t.fir_small_us[:n]],
+            "fir_medium_us": [round(v, 2) for v in t.fir_medium_us[:n]],
             "fir_large_us": [round(v, 2) for v in t.fir_large_us[:n]],
             "assign_per_sm": list(t.assign_per_sm) if n else [],
             "assign_us": [round(v, 2) for v in t.assign_us] if n else []}
@@ -263,15 +265,19 @@ def autotune(H: int, W: int, D: int, device=None) -> dict:
 
 
 def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
-               assign_ctas_per_sm: Optional[int] = None) -> None:
-    """Install launch shapes for (H, W, D) on the current device; with both
-    arguments None the entry is removed (defaults apply again)."""
-    if fir_small_below is None and assign_ctas_per_sm is None:
+               assign_ctas_per_sm: Optional[int] = None,
+               fir_medium_below: Optional[int] = None) -> None:
+    """Install launch shapes for (H, W, D) on the current device; with every
+    argument None the entry is removed (defaults apply again).  A radius r
+    takes the 32-row FIR tiling when r < fir_small_below, else the 64-row one
+    when r < fir_medium_below, else the 128-row one."""
+    if fir_small_below is None and assign_ctas_per_sm is None and fir_medium_below is None:
         check(load().plas_set_tuning(H, W, D, None), "plas_set_tuning")
         return
     cur = get_tuning(H, W, D)
     t = _lib.plas_tuning()
     t.fir_small_below = cur["fir_small_below"] if fir_small_below is None else fir_small_below
+    t.fir_medium_below = cur["fir_medium_below"] if fir_medium_below is None else fir_medium_below
     t.assign_ctas_per_sm = (cur["assign_ctas_per_sm"] if assign_ctas_per_sm is None
                             else assign_ctas_per_sm)
     check(load().plas_set_tuning(H, W, D, ctypes.byref(t)), "plas_set_tuning")

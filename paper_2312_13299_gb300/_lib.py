@@ -68,8 +68,10 @@ TUNE_ASSIGN_CANDIDATES = 4
 
 
 class plas_tuning(ctypes.Structure):
-    _fields_ = [("fir_small_below", c_int), ("assign_ctas_per_sm", c_int), ("n_radii", c_int),
+    _fields_ = [("fir_small_below", c_int), ("fir_medium_below", c_int),
+                ("assign_ctas_per_sm", c_int), ("n_radii", c_int),
                 ("radius", c_int * TUNE_MAX_RADII), ("fir_small_us", c_float * TUNE_MAX_RADII),
+                ("fir_medium_us", c_float * TUNE_MAX_RADII),
                 ("fir_large_us", c_float * TUNE_MAX_RADII),
                 ("assign_per_sm", c_int * TUNE_ASSIGN_CANDIDATES),
                 ("assign_us", c_float * TUNE_ASSIGN_CANDIDATES)]

@@ -55,7 +55,7 @@ struct Slot {
     long long N = 0;
     int nlev = 0;
     int ctas[kClsCount] = {0, 0, 0};
-    int small_below = kDefaultSmallBelow;  // FIR tiling choice (one-grid sweeps)
+    Tuning tune;  // FIR tiling choice (one-grid sweeps)
     bool active = false;
     DevState last{};
     long long last_it = -1;
@@ -171,7 +171,7 @@ class Engine {
         launches_ += 5;
         if (int e = check_launch("preparation")) return e;
         const Tuning tu = tuning_for(H, W, D_);
-        sl->small_below = tu.small_below;
+        sl->tune = tu;
         sl->ctas[kClsFirY] = fir_ctas(H, W * D_, kFirLargeRadius);
         sl->ctas[kClsFirX] = fir_ctas(W, H * D_, kFirLargeRadius);
         sl->ctas[kClsAssign] = assign_ctas(H, W, nsm_, tu.assign_per_sm);
@@ -191,7 +191,7 @@ class Engine {
         p.k = k;
         const bool one = active_.size() == 1;
         p.grids = one ? active_[0]->ws.ref : dgrids_;
-        // FIR tiling: one grid follows the radius it last reported (both tilings
+        // FIR tiling: one grid follows the radius it last reported (all tilings
         // give the same bits; a stale choice only costs time); many grids use
         // the large-radius tiling their CTA maps were built for
         p.var = kFirLargeRadius;
@@ -202,7 +202,7 @@ class Engine {
         if (one) {
             const Slot* sl = active_[0];
             const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
-            p.var = sl->geo.lv[L].r < sl->small_below ? kFirSmallRadius : kFirLargeRadius;
+            p.var = fir_tiling(sl->geo.lv[L].r, sl->tune);
             p.ctas[kClsFirY] = fir_ctas(sl->job.H, sl->job.W * D_, p.var);
             p.ctas[kClsFirX] = fir_ctas(sl->job.W, sl->job.H * D_, p.var);
         }
@@ -498,7 +498,7 @@ class Engine {
     std::vector<EventPair> marks_;
     std::vector<cudaEvent_t> pool_;
     cudaStream_t cap_ = nullptr;
-    Graph graph_[2];  // one per FIR tiling
+    Graph graph_[kFirTilings];  // one per FIR tiling
     bool graphs_failed_ = false;
 
    public:
@@ -761,7 +761,7 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
         sl.mem = ws;
         if (int e = eng.admit(&sl)) return e;
         out->radius[i] = r;
-        for (int var : {kFirLargeRadius, kFirSmallRadius}) {
+        for (int var : {kFirLargeRadius, kFirMediumRadius, kFirSmallRadius}) {
             const int c0 = fir_ctas(H, W * D, var), c1 = fir_ctas(W, H * D, var);
             float us = 0.0f;
             if (int e = time_us(st, a, b, kReps, [&] {
@@ -769,7 +769,8 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
                     launch_fir(1, sl.ws.ref, nullptr, c1, D, var, st);
                 }, &us))
                 return e;
-            (var == kFirSmallRadius ? out->fir_small_us : out->fir_large_us)[i] = us;
+            (var == kFirSmallRadius ? out->fir_small_us
+             : var == kFirMediumRadius ? out->fir_medium_us : out->fir_large_us)[i] = us;
         }
         for (int k = 0; k < 2; ++k) {
             if (r != assign_r[k] || (k == 1 && assign_r[1] == assign_r[0])) continue;
@@ -784,17 +785,25 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
             }
         }
     }
-    // the threshold that minimises the summed time over the measured radii
-    int best_t = 1;
+    // the two thresholds (small <= medium) that minimise the summed time over
+    // the measured radii
+    Tuning best;
     double best_cost = -1.0;
     for (size_t j = 0; j <= radii.size(); ++j) {
-        const int t = j < radii.size() ? radii[j] : rtop + 1;
-        double cost = 0.0;
-        for (size_t i = 0; i < radii.size(); ++i)
-            cost += radii[i] < t ? out->fir_small_us[i] : out->fir_large_us[i];
-        if (best_cost < 0.0 || cost < best_cost) {
-            best_cost = cost;
-            best_t = t;
+        for (size_t m = j; m <= radii.size(); ++m) {
+            Tuning t;
+            t.small_below = j < radii.size() ? radii[j] : rtop + 1;
+            t.medium_below = m < radii.size() ? radii[m] : rtop + 1;
+            double cost = 0.0;
+            for (size_t i = 0; i < radii.size(); ++i) {
+                const int v = fir_tiling(radii[i], t);
+                cost += v == kFirSmallRadius ? out->fir_small_us[i]
+                        : v == kFirMediumRadius ? out->fir_medium_us[i] : out->fir_large_us[i];
+            }
+            if (best_cost < 0.0 || cost < best_cost) {
+                best_cost = cost;
+                best = t;
+            }
         }
     }
     int best_c = 0;
@@ -803,10 +812,10 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
         out->assign_us[c] = assign_us[c];
         if (assign_us[c] < assign_us[best_c]) best_c = c;
     }
-    out->fir_small_below = best_t;
+    out->fir_small_below = best.small_below;
+    out->fir_medium_below = best.medium_below;
     out->assign_ctas_per_sm = per_sm[best_c];
-    Tuning tu;
-    tu.small_below = best_t;
+    Tuning tu = best;
     tu.assign_per_sm = per_sm[best_c];
     install_tuning(H, W, D, &tu);
     return PLAS_OK;

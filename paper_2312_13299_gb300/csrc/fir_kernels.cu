@@ -30,10 +30,12 @@ namespace plas {
 
 static_assert(kFirCols == 128, "four columns per lane");
 
-// Two tilings of the same kernel (identical results): rows per CTA, ring rows,
-// tap steps per chunk.  The large one keeps 16 warps per CTA busy at large
-// radii; the small one (4 CTAs per SM) overlaps the short load / compute /
-// store phases of small radii across CTAs.
+// Three tilings of the same kernel (identical results): rows per CTA, ring
+// rows, tap steps per chunk, CTAs per SM.  The large one keeps 16 warps per
+// CTA busy at large radii; the medium one (2 CTAs per SM) overlaps one CTA's
+// first fetch and epilogue with the other's taps at middle radii; the small
+// one (4 CTAs per SM) overlaps the short load / compute / store phases of
+// small radii across CTAs.
 template <int TY_, int RING_, int CH_, int MINB_>
 struct FirTiling {
     static constexpr int TY = TY_, RING = RING_, CH = CH_, MINB = MINB_;
@@ -46,6 +48,7 @@ struct FirTiling {
     }
 };
 using FirLarge = FirTiling<128, 256, 56, 1>;
+using FirMedium = FirTiling<64, 128, 24, 2>;
 using FirSmall = FirTiling<32, 64, 8, 4>;
 
 __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
@@ -280,7 +283,8 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
 }
 
 int fir_ctas(int rows, int cols, int variant) {
-    const int ty = variant == kFirSmallRadius ? FirSmall::TY : FirLarge::TY;
+    const int ty = variant == kFirSmallRadius ? FirSmall::TY
+                   : variant == kFirMediumRadius ? FirMedium::TY : FirLarge::TY;
     return ((cols + kFirCols - 1) / kFirCols) * ((rows + ty - 1) / ty);
 }
 
@@ -294,6 +298,8 @@ static void fir_opt_in() {
     if (dev < 0 || dev >= 64 || done[dev]) return;
     cudaFuncSetAttribute(fir_kernel<FirLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fir_smem<FirLarge>());
+    cudaFuncSetAttribute(fir_kernel<FirMedium>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fir_smem<FirMedium>());
     cudaFuncSetAttribute(fir_kernel<FirSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fir_smem<FirSmall>());
     done[dev] = true;
@@ -307,6 +313,9 @@ void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int
     fir_opt_in();
     if (variant == kFirSmallRadius)
         fir_kernel<FirSmall><<<ctas, FirSmall::THREADS, fir_smem<FirSmall>(), s>>>(
+            pass, grids, map, D, grid_stride(D), target_stride(D));
+    else if (variant == kFirMediumRadius)
+        fir_kernel<FirMedium><<<ctas, FirMedium::THREADS, fir_smem<FirMedium>(), s>>>(
             pass, grids, map, D, grid_stride(D), target_stride(D));
     else
         fir_kernel<FirLarge><<<ctas, FirLarge::THREADS, fir_smem<FirLarge>(), s>>>(

@@ -264,11 +264,14 @@ int plas_set_tuning(int H, int W, int D, const plas_tuning* t) {
         install_tuning(H, W, D, nullptr);
         return PLAS_OK;
     }
-    if (t->fir_small_below < 0 || t->assign_ctas_per_sm < 1 || t->assign_ctas_per_sm > kAssignMaxPerSm)
-        return fail(PLAS_ERR_INVALID_ARG, "fir_small_below must be >= 0, assign_ctas_per_sm 1..%d",
+    if (t->fir_small_below < 0 || t->fir_medium_below < 0 || t->assign_ctas_per_sm < 1 ||
+        t->assign_ctas_per_sm > kAssignMaxPerSm)
+        return fail(PLAS_ERR_INVALID_ARG,
+                    "fir_small_below and fir_medium_below must be >= 0, assign_ctas_per_sm 1..%d",
                     kAssignMaxPerSm);
     Tuning tu;
     tu.small_below = t->fir_small_below;
+    tu.medium_below = t->fir_medium_below;
     tu.assign_per_sm = t->assign_ctas_per_sm;
     install_tuning(H, W, D, &tu);
     return PLAS_OK;
@@ -281,6 +284,7 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out) {
     memset(out, 0, sizeof(*out));
     const Tuning t = tuning_for(H, W, D);
     out->fir_small_below = t.small_below;
+    out->fir_medium_below = t.medium_below;
     out->assign_ctas_per_sm = t.assign_per_sm;
     return PLAS_OK;
 }
@@ -412,7 +416,7 @@ static int target_impl(const float* x, int H, int W, int D, const float* weights
         if (mode == 1) {
             launch_box_target(ws.ref, H, W, D, num_sms(), st);
         } else {
-            const int var = g.lv[0].r < tuning_for(H, W, D).small_below ? kFirSmallRadius : kFirLargeRadius;
+            const int var = fir_tiling(g.lv[0].r, tuning_for(H, W, D));
             launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st);
             launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st);
         }

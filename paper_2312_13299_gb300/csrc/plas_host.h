@@ -71,12 +71,17 @@ size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 // What a sort of this shape on the current device uses: the installed entry
 // for (D, H, W), else the entry with the same D and the nearest cell count,
 // else the defaults.
-constexpr int kDefaultSmallBelow = 24;
+constexpr int kDefaultSmallBelow = 1;
+constexpr int kDefaultMediumBelow = 96;
 constexpr int kDefaultAssignPerSm = 8;
 struct Tuning {
-    int small_below = kDefaultSmallBelow;
+    int small_below = kDefaultSmallBelow;    // 32-row FIR tiling below this radius
+    int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row
     int assign_per_sm = kDefaultAssignPerSm;
 };
+inline int fir_tiling(int r, const Tuning& t) {
+    return r < t.small_below ? kFirSmallRadius : r < t.medium_below ? kFirMediumRadius : kFirLargeRadius;
+}
 Tuning tuning_for(int H, int W, int D);
 void install_tuning(int H, int W, int D, const Tuning* t);  // nullptr removes
 

@@ -20,7 +20,7 @@ constexpr int kMaxD = 64;
 constexpr int kFirX = 8;       // outputs per lane and column of the FIR passes
 constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
 // FIR tilings (identical results); which one a radius uses is a tuning choice
-constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1;
+constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1, kFirMediumRadius = 2, kFirTilings = 3;
 constexpr int kAssignThreads = 256;
 
 struct Weights {

@@ -43,19 +43,27 @@ def test_library_is_sm103a_only():
     assert "-fmad=false" in build.NVFLAGS
 
 
+# (fir_small_below, fir_medium_below, assign_ctas_per_sm) when nothing is installed
+DEFAULT_TUNING = (1, 96, 8)
+
+
 def test_tuning_table_round_trip_host_only():
     """The launch-shape table is host state: install, look up (nearest cell
     count for the same D), validate and remove -- no device work."""
     import paper_2312_13299_gb300 as plas
-    plas.set_tuning(64, 64, 5, fir_small_below=7, assign_ctas_per_sm=3)
+    plas.set_tuning(64, 64, 5, fir_small_below=7, fir_medium_below=40, assign_ctas_per_sm=3)
     try:
         t = plas.get_tuning(64, 64, 5)
-        assert (t["fir_small_below"], t["assign_ctas_per_sm"]) == (7, 3)
+        assert (t["fir_small_below"], t["fir_medium_below"], t["assign_ctas_per_sm"]) == (7, 40, 3)
         assert plas.get_tuning(70, 60, 5)["fir_small_below"] == 7   # nearest entry, same D
-        assert plas.get_tuning(64, 64, 6)["fir_small_below"] == 24  # other D: defaults
+        d = plas.get_tuning(64, 64, 6)                              # other D: defaults
+        assert (d["fir_small_below"], d["fir_medium_below"], d["assign_ctas_per_sm"]) == (
+            DEFAULT_TUNING)
         import pytest
         with pytest.raises(RuntimeError):
             plas.set_tuning(64, 64, 5, assign_ctas_per_sm=17)
+        with pytest.raises(RuntimeError):
+            plas.set_tuning(64, 64, 5, fir_medium_below=-1)
     finally:
         plas.set_tuning(64, 64, 5)
     assert plas.get_tuning(64, 64, 5)["assign_ctas_per_sm"] == 8
