@@ -126,6 +126,7 @@ def lib():
             L.orc_grid_select.restype = i
             L.orc_quantize.argtypes = [f, ctypes.c_long, i, f, f, P(i),
                                        P(ctypes.c_ushort)]
+            L.orc_dequantize.argtypes = [P(ctypes.c_ushort), ctypes.c_long, i, f, f, P(i), f]
             L.orc_num_threads.restype = i
             _lib = L
     return _lib
@@ -366,6 +367,19 @@ def quantize(x: np.ndarray, lo, hi, q) -> np.ndarray:
     lib().orc_quantize(_p(x, ctypes.c_float), n, C, _p(lo_a, ctypes.c_float),
                        _p(hi_a, ctypes.c_float), _p(q_a, ctypes.c_int),
                        _p(out, ctypes.c_ushort))
+    return out
+
+
+def dequantize(codes: np.ndarray, lo, hi, q) -> np.ndarray:
+    """Sec. 3.3: the float32 value of each code of an [N, C] uint16 array."""
+    codes = np.ascontiguousarray(codes, np.uint16)
+    C = codes.shape[-1]
+    n = codes.size // C
+    lo_a, hi_a = _f32(lo), _f32(hi)
+    q_a = np.ascontiguousarray(q, np.int32)
+    out = np.zeros(codes.shape, np.float32)
+    lib().orc_dequantize(_p(codes, ctypes.c_ushort), n, C, _p(lo_a, ctypes.c_float),
+                         _p(hi_a, ctypes.c_float), _p(q_a, ctypes.c_int), _p(out, ctypes.c_float))
     return out
 
 

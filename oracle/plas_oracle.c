@@ -831,6 +831,19 @@ void orc_quantize(const float* x, long n, int C, const float* lo, const float* h
     }
 }
 
+/* The value a code stands for (the inverse step of Sec. 3.3): level k of
+ * channel c is lo_c + k * ((hi_c - lo_c) / (q_c - 1)) in FP32 (lo_c when the
+ * range is degenerate). */
+void orc_dequantize(const unsigned short* codes, long n, int C, const float* lo, const float* hi,
+                    const int* q, float* out)
+{
+    for (long i = 0; i < n * C; ++i) {
+        const int c = (int)(i % C);
+        const float step = hi[c] > lo[c] ? (hi[c] - lo[c]) / (float)(q[c] - 1) : 0.0f;
+        out[i] = lo[c] + (float)codes[i] * step;
+    }
+}
+
 /* Activation of raw 3DGS parameters into the sort features (Sec. 3.1: the
  * sort uses the values the renderer sees; Sec. 3.3: coordinates go through
  * x = sign(v) (exp(|v|) - 1)).  Row layout of raw (stride floats apart):
