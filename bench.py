@@ -642,6 +642,63 @@ def run_threshold_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stages(args):
+    """Preparation before the sort (Sec. 3.1, Sec. 3.3) and quantisation
+    after it (Sec. 3.3) on 1,100,000 raw Gaussians of 59 channels (14 sort +
+    45 carried; N(0, 1.5) values, seed 0): activation of the 14 sort
+    channels, largest-square selection on the opacity logits (channel 10, a
+    strided column), row selection of the kept 1048^2 Gaussians, and their
+    quantisation to 16-bit codes (q = 65536 for xyz, 256 otherwise) and back.
+    Each stage is timed with CUDA events over 10*K calls after W warm-ups.
+    Algorithmic bytes per call: activation 56 B read + 56 B written per
+    Gaussian; selection 4 B read per Gaussian + 4 B written per kept one;
+    row selection 236 B read + 236 B written + 4 B index per kept row;
+    (de)quantisation 4 + 2 B per element."""
+    import torch
+    import paper_2312_13299_gb300 as plas
+    plas.load()
+    n, C = 1_100_000, 59
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    raw = torch.randn((n, C), generator=gen, device="cuda") * 1.5
+    side, keep = plas.grid_select(raw[:, 10])
+    kept = plas.select_rows(raw, keep)
+    lo = kept.min(dim=0).values.cpu().tolist()
+    hi = kept.max(dim=0).values.cpu().tolist()
+    q = [65536] * 3 + [256] * (C - 3)
+    codes = plas.quantize(kept, lo, hi, q)
+    peaks, psrc = _peaks()
+    m = side * side
+    stages = [("activate_3dgs", lambda: plas.activate_3dgs(raw), 112 * n),
+              ("grid_select", lambda: plas.grid_select(raw[:, 10]), 4 * n + 4 * m),
+              ("select_rows", lambda: plas.select_rows(raw, keep), m * (8 * C + 4)),
+              ("quantize", lambda: plas.quantize(kept, lo, hi, q), 6 * m * C),
+              ("dequantize", lambda: plas.dequantize(codes, lo, hi, q), 6 * m * C)]
+    out = {}
+    for name, fn, nbytes in stages:
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = args.steps * 10
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        gbs = nbytes / (us * 1e-6) / 1e9
+        out[name] = {"us": round(us, 2), "bytes": int(nbytes), "GB/s": round(gbs, 1),
+                     "frac": round(gbs / peaks["hbm_gbs"], 3)}
+    line = {"metric": "preparation and quantisation kernels, 1.1M raw Gaussians x 59 channels",
+            "unit": "us per call", "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic N(0, 1.5) raw parameters", "side": side,
+            "peak_hbm_gbs": peaks["hbm_gbs"], "peak_source": psrc,
+            "timing": "CUDA events over 10*K back-to-back calls (inputs 260 MB > L2)",
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(args):
     """A bounded launch sequence for profiler captures: the workload's inputs,
     one sort capped at --ncu-case iterations (all at the top radius levels)."""
@@ -691,6 +748,8 @@ def main():
                          "own JSON line (use with --workload p0)")
     ap.add_argument("--tols", default="1e-2,3e-3,1e-3,3e-4,1e-4,3e-5,1e-5",
                     help="with --threshold-sweep: the thresholds")
+    ap.add_argument("--stages", action="store_true",
+                    help="preparation and quantisation kernel benchmark, own JSON line")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
     ap.add_argument("--policies", default="fifo_fill,shortest_first,all",
@@ -708,6 +767,9 @@ def main():
         return
     if args.threshold_sweep:
         run_threshold_sweep(args)
+        return
+    if args.stages:
+        run_stages(args)
         return
     if args.impl == "reference":
         run_reference(args)

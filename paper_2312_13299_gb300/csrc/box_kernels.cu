@@ -3,13 +3,19 @@
 // arXiv 2312.13299): the mean of the in-range cells of the (2r+1) x (2r+1)
 // window around each cell, on fixed-point features q = rint(F 2^s).
 //
-// The window sums are exact int64 arithmetic, so they come from a summed-area
-// table I(y, x) = sum_{y' <= y, x' <= x} q: a scan along x per (row,
-// channel), a scan along y per (column, channel), then four corner reads
-// per output.  The cost does not depend on r.  Each output is
-//   T = ((float)S / (float)n) * 2^-s   (FP32, IEEE division),
-// the same bits as the oracle's sliding window sums.  The evaluation launch
-// also writes the iteration's grouping table.
+// The window sums are exact int64 arithmetic, so any order of summation gives
+// the same sums, and the cost does not depend on r.  Two launches:
+//   1. column prefix sums P(y, x) = sum_{y' <= y} q(y', x), read straight
+//      from the working grid (one CTA per cell column);
+//   2. per (row, channel pair): the window's column sums
+//      V(x) = P(y+r, x) - P(y-r-1, x) (rows clipped to the grid), their
+//      prefix along x in shared memory, S(x) = R(x+r) - R(x-r-1) and
+//      T = ((float)S / (float)n) * 2^-s   (FP32, IEEE division);
+//      this launch also writes the iteration's grouping table.
+// The same bits as the oracle's sliding window sums.  Rows wider than
+// kRowsMaxW cells (whose prefix does not fit in shared memory) take a
+// three-launch path over a full summed-area table I(y, x) instead: a scan
+// along x, a scan along y, four corner reads per output.
 #include <algorithm>
 
 #include "plas_kernels.h"
@@ -20,6 +26,8 @@ namespace {
 
 constexpr int kScanThreads = 256;
 constexpr int kEvalThreads = 256;
+constexpr int kRowThreads = 256;
+constexpr int kRowsMaxW = 6144;  // prefix of one channel pair of a row: 16 B per cell, <= 96 KB
 
 __device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }  // exact for |e| <= 126
 
@@ -202,6 +210,186 @@ __global__ void __launch_bounds__(kEvalThreads) box_eval_kernel(const GridRef* _
     write_group_table(gr, lv, st, blockIdx.x, gridDim.x, kEvalThreads);
 }
 
+// column prefix sums of q = rint(F 2^s), read from the working grid: one CTA
+// per cell column; thread (k, j) owns row segment k of channel pair j (8-byte
+// loads of the pair's features, 16-byte stores of the pair's sums).  Phase 1
+// sums the segments, phase 2 scans the segment totals per pair, phase 3
+// walks the segments again (one cell column is H x 4 gs bytes, mostly cache-
+// resident) and writes P(y, x) = sum_{y' <= y} q(y', x).
+__global__ void __launch_bounds__(kScanThreads) box_colprefix_kernel(const GridRef* __restrict__ grids, int D,
+                                                                     int gs) {
+    __shared__ longlong2 tot[kScanThreads];
+    const GridRef& gr = grids[0];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const int H = gr.H, W = gr.W, x = blockIdx.x;
+    const int pairs = sat_channels(D) / 2;
+    const int K = kScanThreads / pairs;
+    const int L = (H + K - 1) / K;
+    const int t = threadIdx.x, k = t / pairs, j = t - (t / pairs) * pairs;
+    const bool act = k < K;
+    const bool two = 2 * j + 1 < D;  // else the pair's second channel is the zero pad
+    const int y0 = min(k * L, H), y1 = min(y0 + L, H);
+    const float scale = pow2f(st->box_exp);
+    const long long grow = (long long)W * gs;  // floats per grid row
+    const float* g = gr.G + (long long)x * gs + 2 * j;
+    // read-only loads (the grid is not written by this launch), so they can
+    // be issued ahead of the stores of phase 3
+    auto q2 = [&](int y) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(g + (long long)y * grow));
+        return make_longlong2(__float2ll_rn(__fmul_rn(f.x, scale)),
+                              two ? __float2ll_rn(__fmul_rn(f.y, scale)) : 0LL);
+    };
+    long long s0 = 0, s1 = 0;
+    if (act) {
+        int y = y0;
+        for (; y + 4 <= y1; y += 4) {
+            const longlong2 a = q2(y), b = q2(y + 1), c = q2(y + 2), e = q2(y + 3);
+            s0 += a.x + b.x + c.x + e.x;
+            s1 += a.y + b.y + c.y + e.y;
+        }
+        for (; y < y1; ++y) {
+            const longlong2 a = q2(y);
+            s0 += a.x;
+            s1 += a.y;
+        }
+    }
+    tot[t] = make_longlong2(s0, s1);
+    __syncthreads();
+    if (t < pairs) {
+        long long r0 = 0, r1 = 0;
+        for (int kk = 0; kk < K; ++kk) {
+            const longlong2 v = tot[kk * pairs + t];
+            tot[kk * pairs + t] = make_longlong2(r0, r1);
+            r0 += v.x;
+            r1 += v.y;
+        }
+    }
+    __syncthreads();
+    if (act) {
+        long long r0 = tot[t].x, r1 = tot[t].y;
+        longlong2* p = reinterpret_cast<longlong2*>(gr.sat) + (long long)x * pairs + j;
+        const long long row = (long long)W * pairs;  // longlong2 per row
+        int y = y0;
+        for (; y + 4 <= y1; y += 4) {
+            longlong2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = q2(y + u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                r0 += v[u].x;
+                r1 += v[u].y;
+                p[(long long)(y + u) * row] = make_longlong2(r0, r1);
+            }
+        }
+        for (; y < y1; ++y) {
+            const longlong2 a = q2(y);
+            r0 += a.x;
+            r1 += a.y;
+            p[(long long)y * row] = make_longlong2(r0, r1);
+        }
+    }
+}
+
+// one CTA per (row y, channel pair j): the window's column sums
+// V(x) = P(min(y+r, H-1), x) - P(y-r-1, x), their inclusive prefix R along x
+// in shared memory (thread t owns cells [t*cpt, (t+1)*cpt); the thread totals
+// are scanned with warp shuffles), then per cell S = R(min(x+r, W-1)) -
+// R(x-r-1) and the target.  The CTAs of one row's channel pairs are adjacent,
+// so the 16-byte loads of one pair share their lines with the others in L2.
+__global__ void __launch_bounds__(kRowThreads) box_rows_kernel(const GridRef* __restrict__ grids, int D, int ts) {
+    extern __shared__ longlong2 R[];  // W entries
+    __shared__ longlong2 wsum[kRowThreads / 32];
+    const GridRef& gr = grids[0];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const LevelDesc& lv = gr.lv[st->level];
+    const int H = gr.H, W = gr.W, r = lv.r;
+    const int pairs = sat_channels(D) / 2;
+    const int y = blockIdx.x / pairs, j = blockIdx.x - (blockIdx.x / pairs) * pairs;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int yb = min(y + r, H - 1), ya = y - r - 1;
+    const longlong2* P = reinterpret_cast<const longlong2*>(gr.sat);
+    const longlong2* pb = P + (long long)yb * W * pairs + j;
+    const longlong2* pa = P + (long long)max(ya, 0) * W * pairs + j;
+    const int cpt = (W + kRowThreads - 1) / kRowThreads;
+    const int c0 = min(t * cpt, W), c1 = min(c0 + cpt, W);
+    long long s0 = 0, s1 = 0;
+    // four cells at a time: read-only loads first (P is not written by this
+    // launch), then the prefix into shared memory
+    for (int xb = c0; xb < c1; xb += 4) {
+        longlong2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = make_longlong2(0, 0);
+            if (xb + u < c1) {
+                v[u] = __ldg(pb + (long long)(xb + u) * pairs);
+                if (ya >= 0) {
+                    const longlong2 a = __ldg(pa + (long long)(xb + u) * pairs);
+                    v[u].x -= a.x;
+                    v[u].y -= a.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (xb + u < c1) {
+                s0 += v[u].x;
+                s1 += v[u].y;
+                R[xb + u] = make_longlong2(s0, s1);
+            }
+        }
+    }
+    // exclusive prefix of the thread totals across the CTA
+    long long e0 = s0, e1 = s1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u0 = shfl_up64(e0, o), u1 = shfl_up64(e1, o);
+        if (lane >= o) {
+            e0 += u0;
+            e1 += u1;
+        }
+    }
+    if (lane == 31) wsum[warp] = make_longlong2(e0, e1);
+    e0 -= s0;
+    e1 -= s1;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) {
+        e0 += wsum[w].x;
+        e1 += wsum[w].y;
+    }
+    for (int x = c0; x < c1; ++x) {
+        longlong2 v = R[x];
+        v.x += e0;
+        v.y += e1;
+        R[x] = v;
+    }
+    __syncthreads();
+    const int ny = yb - max(y - r, 0) + 1;
+    const float inv_scale = pow2f(-st->box_exp);
+    const bool two = 2 * j + 1 < D;
+    // the last pair's CTA also zero-fills the target's pad channels, so that
+    // every 32-byte sector of a target line is written in full
+    const int pad0 = 2 * pairs, pad1 = j == pairs - 1 ? ts : pad0;
+    float* out = gr.T + (long long)y * W * ts;
+    for (int x = t; x < W; x += kRowThreads) {
+        const int xb = min(x + r, W - 1), xa = x - r - 1;
+        longlong2 S = R[xb];
+        if (xa >= 0) {
+            const longlong2 a = R[xa];
+            S.x -= a.x;
+            S.y -= a.y;
+        }
+        const float n = (float)(ny * (xb - max(x - r, 0) + 1));
+        float* o = out + (long long)x * ts;
+        const float v0 = __fmul_rn(__fdiv_rn(__ll2float_rn(S.x), n), inv_scale);
+        const float v1 = two ? __fmul_rn(__fdiv_rn(__ll2float_rn(S.y), n), inv_scale) : 0.0f;
+        *reinterpret_cast<float2*>(o + 2 * j) = make_float2(v0, v1);
+        for (int c = pad0; c < pad1; c += 2) *reinterpret_cast<float2*>(o + c) = make_float2(0.0f, 0.0f);
+    }
+    write_group_table(gr, lv, st, blockIdx.x, gridDim.x, kRowThreads);
+}
+
 template <int D>
 void launch_rowscan_t(const GridRef* grid, int H, cudaStream_t s) {
     box_rowscan_kernel<D><<<(unsigned)H, kScanThreads, 0, s>>>(grid);
@@ -235,10 +423,28 @@ void launch_rowscan(const GridRef* grid, int H, int D, cudaStream_t s) {
 
 }  // namespace
 
+void prepare_box_launches() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(box_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(longlong2) * kRowsMaxW));
+    done[dev] = true;
+}
+
 void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cudaStream_t s) {
+    const int pairs = sat_channels(D) / 2;
+    if (W <= kRowsMaxW) {
+        prepare_box_launches();
+        box_colprefix_kernel<<<(unsigned)W, kScanThreads, 0, s>>>(grid, D, grid_stride(D));
+        box_rows_kernel<<<(unsigned)((long long)H * pairs), kRowThreads, sizeof(longlong2) * (size_t)W, s>>>(
+            grid, D, target_stride(D));
+        return;
+    }
     launch_rowscan(grid, H, D, s);                                          // one CTA per row
     box_colscan_kernel<<<(unsigned)W, kScanThreads, 0, s>>>(grid, sat_channels(D));  // per cell column
-    const long long total = (long long)H * W * (sat_channels(D) / 2);
+    const long long total = (long long)H * W * pairs;
     const unsigned blocks = (unsigned)std::min<long long>((total + kEvalThreads - 1) / kEvalThreads,
                                                           (long long)num_sms * 8);
     box_eval_kernel<<<blocks, kEvalThreads, 0, s>>>(grid, D, target_stride(D));

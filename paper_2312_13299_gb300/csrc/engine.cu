@@ -372,6 +372,7 @@ class Engine {
         }
         if (!cap_) PLAS_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
         prepare_fir_launches();
+        prepare_box_launches();
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();

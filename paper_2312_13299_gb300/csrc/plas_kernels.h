@@ -129,6 +129,9 @@ void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, dou
                    cudaStream_t s);
 
 // ---- box target (target_mode 1): one grid -------------------------------------
+// (prepare_box_launches: the shared-memory opt-in, once per device, before a
+// stream capture; launch_box_target calls it too)
+void prepare_box_launches();
 void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cudaStream_t s);
 
 // ---- outputs -----------------------------------------------------------------

@@ -17,8 +17,15 @@ def _cuda(a):
 
 @pytest.mark.parametrize("H,W,D,phi,normalize", [(64, 64, 3, 31.0, True), (37, 53, 5, 7.5, True),
                                                  (128, 96, 14, 47.0, True), (20, 30, 1, 40.0, True),
-                                                 (50, 40, 4, 3.0, False), (8, 200, 2, 1.0, True)])
+                                                 (50, 40, 4, 3.0, False), (8, 200, 2, 1.0, True),
+                                                 (1, 300, 15, 40.0, True), (257, 1, 2, 70.0, True),
+                                                 (33, 70, 64, 12.0, True), (45, 38, 16, 9.0, False),
+                                                 (4, 6144, 3, 100.0, True), (3, 7000, 3, 5.0, True),
+                                                 (2, 9000, 14, 2000.0, True)])
 def test_box_target_bitexact(plas, orc, H, W, D, phi, normalize):
+    """Ragged and degenerate shapes (single row or column, odd D, D = 64),
+    rows up to the shared-memory prefix limit of 6144 cells (two launches)
+    and wider rows (the three-launch summed-area path)."""
     rng = np.random.default_rng(H * W + D)
     x = (rng.standard_normal((H * W, D)) * 3).astype(np.float32)
     perm = rng.permutation(H * W).astype(np.int32)

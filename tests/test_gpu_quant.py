@@ -55,3 +55,26 @@ def test_quantize_rejects_bad_ranges(plas):
         plas.quantize(x, [0.0, 1.0], [1.0, 0.0], [4, 4])
     with pytest.raises(RuntimeError):
         plas.quantize(x, [0.0, 0.0], [1.0, 1.0], [1, 4])
+
+
+@pytest.mark.parametrize("N,C,offset", [(1, 1, 0), (3, 1, 0), (4097, 3, 0), (1001, 7, 1), (300000, 59, 0),
+                                        (999, 256, 0), (2, 5, 3), (70000, 14, 2)])
+def test_quantize_dequantize_bitexact_shapes(plas, orc, N, C, offset):
+    """Both directions bit for bit against the oracle: element counts that
+    are not a multiple of 4, one channel, the maximum of 256 channels, many
+    grid-stride steps, and views that start off a 16-byte boundary (the
+    scalar path)."""
+    rng = np.random.default_rng(N * C + offset)
+    x = rng.normal(0, 2, N * C + offset).astype(np.float32)
+    lo = rng.uniform(-3, 0, C).astype(np.float32)
+    hi = (lo + rng.uniform(0, 4, C)).astype(np.float32)
+    hi[::5] = lo[::5]                                   # degenerate ranges
+    q = rng.integers(2, 65537, C).astype(np.int32)
+    xt = torch.from_numpy(x).cuda()[offset:].view(N, C)
+    xs = x[offset:].reshape(N, C)
+    want = orc.quantize(xs, lo, hi, q)
+    codes = plas.quantize(xt, lo, hi, q)
+    assert np.array_equal((codes.to(torch.int32) & 0xFFFF).cpu().numpy(), want.astype(np.int32))
+    ct = torch.from_numpy(np.concatenate([np.zeros(offset, np.uint16), want.ravel()]).view(np.int16)).cuda()
+    back = plas.dequantize(ct[offset:].view(N, C), lo, hi, q).cpu().numpy()
+    assert np.array_equal(back.view(np.uint32), orc.dequantize(want, lo, hi, q).view(np.uint32))
