@@ -50,7 +50,11 @@ FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
 # Per-launch DRAM traffic of the dominant kernels from committed ncu
 # summaries (profiles/), keyed by the sha1 of the kernel source they were
 # taken on; a stale hash reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/launches_sort_1024x1024x14.md: DRAM read + write per launch of
+    # the target pass along y, averaged over the 6504 such launches of one sort
+    ("blur_cols", "m1"): {"bytes_per_launch": 84955336, "src": "793aa4f395a0"},
+}
 
 
 def _env_int(name, default):
@@ -709,6 +713,10 @@ def run_ncu_case(args):
     side = wl["side"]
     x_np, _ = make_inputs(wl, seed=0)
     x = torch.from_numpy(x_np).cuda()
+    if args.tune != "auto":  # pinned launch shapes (the default shapes otherwise)
+        sb, mb, per = (int(v) for v in args.tune.split(","))
+        plas.set_tuning(side, side, wl["D"], fir_small_below=sb, fir_medium_below=mb,
+                        assign_ctas_per_sm=per)
     r = plas.sort(x, side, side, seed=0,
                   schedule=plas.Schedule(max_iters=args.ncu_case, phi0=args.phi0,
                                          target_mode=1 if args.target == "box" else 0),

@@ -432,8 +432,8 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
 /*
  * Launch shapes the sort can choose without changing any result: the FIR
  * tiling of the target passes (128 rows per CTA with 16 warps, 64 rows with
- * 2 CTAs per SM, or 32 rows with 4 CTAs per SM; the same FMA chains in every
- * case) and the
+ * 2 CTAs per SM, or 32 rows per CTA loaded straight into registers without
+ * shared memory; the same FMA chains in every case) and the
  * number of assignment CTAs (the residual sum is exact and order-free).  The
  * paper has no counterpart; it is GPU plumbing.
  *
@@ -447,7 +447,7 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   PLAS_ERR_INVALID_ARG for unsupported sizes.
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
- *   shape on the current device would use (the defaults 1, 96 and 8 when
+ *   shape on the current device would use (the defaults 8, 96 and 8 when
  *   nothing is installed).  A radius r takes the 32-row tiling when
  *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
  *   the 128-row one.  Thread-safe.
@@ -460,7 +460,8 @@ typedef struct plas_tuning {
     int assign_ctas_per_sm; /* cap on assignment CTAs per SM, 1..16           */
     int n_radii;            /* radii measured by plas_autotune                */
     int radius[PLAS_TUNE_MAX_RADII];
-    float fir_small_us[PLAS_TUNE_MAX_RADII];  /* both passes, 32-row tiling   */
+    float fir_small_us[PLAS_TUNE_MAX_RADII];  /* both passes, 32-row direct;
+                                                 -1: not timed (r > 32)       */
     float fir_medium_us[PLAS_TUNE_MAX_RADII]; /* both passes, 64-row tiling   */
     float fir_large_us[PLAS_TUNE_MAX_RADII];  /* both passes, 128-row tiling  */
     int assign_per_sm[PLAS_TUNE_ASSIGN_CANDIDATES];

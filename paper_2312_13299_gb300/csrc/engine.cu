@@ -763,6 +763,10 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
         if (int e = eng.admit(&sl)) return e;
         out->radius[i] = r;
         for (int var : {kFirLargeRadius, kFirMediumRadius, kFirSmallRadius}) {
+            if (var == kFirSmallRadius && r > kDirectTuneMaxR) {  // correct, but slow there
+                out->fir_small_us[i] = -1.0f;
+                continue;
+            }
             const int c0 = fir_ctas(H, W * D, var), c1 = fir_ctas(W, H * D, var);
             float us = 0.0f;
             if (int e = time_us(st, a, b, kReps, [&] {
@@ -798,8 +802,9 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
             double cost = 0.0;
             for (size_t i = 0; i < radii.size(); ++i) {
                 const int v = fir_tiling(radii[i], t);
-                cost += v == kFirSmallRadius ? out->fir_small_us[i]
-                        : v == kFirMediumRadius ? out->fir_medium_us[i] : out->fir_large_us[i];
+                const float us = v == kFirSmallRadius ? out->fir_small_us[i]
+                                 : v == kFirMediumRadius ? out->fir_medium_us[i] : out->fir_large_us[i];
+                cost += us < 0.0f ? 1e30 : us;  // not measured: never chosen
             }
             if (best_cost < 0.0 || cost < best_cost) {
                 best_cost = cost;

@@ -9,7 +9,9 @@
 // (y, d); output = the target [y][x][d]).  The pass-0 launch also writes the
 // iteration's grouping table (one launch fewer per iteration).
 //
-// A CTA owns 128 columns and TY output rows (128 or 32, see FirTiling).  Lane l handles the four
+// The ring kernel: a CTA owns 128 columns and TY output rows (128 or 64, see
+// FirTiling); small radii use fir_direct_kernel (no ring, 32 rows x 64
+// columns per CTA).  Lane l handles the four
 // columns c0+l, c0+32+l, c0+64+l, c0+96+l as two packed pairs, so each tap step
 // is 16 fma.rn.f32x2 (two independent IEEE round-to-nearest FMAs each) fed by
 // one 16-byte shared-memory load; warp q owns output rows 8q..8q+7 and keeps
@@ -30,12 +32,11 @@ namespace plas {
 
 static_assert(kFirCols == 128, "four columns per lane");
 
-// Three tilings of the same kernel (identical results): rows per CTA, ring
+// Two tilings of the ring kernel (identical results): rows per CTA, ring
 // rows, tap steps per chunk, CTAs per SM.  The large one keeps 16 warps per
 // CTA busy at large radii; the medium one (2 CTAs per SM) overlaps one CTA's
-// first fetch and epilogue with the other's taps at middle radii; the small
-// one (4 CTAs per SM) overlaps the short load / compute / store phases of
-// small radii across CTAs.
+// first fetch and epilogue with the other's taps at middle radii.  Small
+// radii take fir_direct_kernel below (no ring).
 template <int TY_, int RING_, int CH_, int MINB_>
 struct FirTiling {
     static constexpr int TY = TY_, RING = RING_, CH = CH_, MINB = MINB_;
@@ -49,7 +50,6 @@ struct FirTiling {
 };
 using FirLarge = FirTiling<128, 256, 56, 1>;
 using FirMedium = FirTiling<64, 128, 24, 2>;
-using FirSmall = FirTiling<32, 64, 8, 4>;
 
 __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
                                                     unsigned long long c) {
@@ -282,9 +282,140 @@ __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
     if (pass == 0) write_group_table(gr, lv, st, cr.local, cr.count, kFirThreads);
 }
 
+// Small radii: a kernel without shared memory or barriers.  A CTA of 4 warps
+// owns 32 output rows x 64 columns; warp q owns rows 8q..8q+7 and lane l the
+// columns c0+l and c0+32+l as one packed pair.  The warp loads every input row
+// that its tap steps reach straight into registers with read-only loads (L2
+// serves the rows that neighbouring warps share) and then runs the same
+// ascending FMA chains as the ring kernel: step s of output row i is input
+// row base + s + i.  Up to three 8-step blocks are unrolled with all loads
+// issued first; longer step ranges run block by block, in the same order.
+constexpr int kDirTY = 32, kDirCols = 64, kDirThreads = 128;
+
+template <int NB>
+__device__ __forceinline__ void dir_chains(const float* __restrict__ in, long long in_row,
+                                           const long long (&inoff)[2], const bool (&ok)[2], int R,
+                                           int base, const float2* __restrict__ tp,
+                                           float2 (&acc)[kFirX]) {
+    constexpr int X = kFirX, NR = NB * X + X - 1;
+    float2 w[NR];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) {
+        const int yy = base + m;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (yy >= 0 && yy < R) {  // warp-uniform
+            const float* p = in + (long long)yy * in_row;
+            if (ok[0]) v.x = __ldg(p + inoff[0]);
+            if (ok[1]) v.y = __ldg(p + inoff[1]);
+        }
+        w[m] = v;
+    }
+#pragma unroll
+    for (int s = 0; s < NB * X; ++s) {
+        const float2 k = __ldg(tp + s);
+#pragma unroll
+        for (int i = 0; i < X; ++i) acc[i] = __ffma2_rn(k, w[s + i], acc[i]);
+    }
+}
+
+__global__ void __launch_bounds__(kDirThreads) fir_direct_kernel(
+    int pass, const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, int D, int gs,
+    int ts) {
+    constexpr int X = kFirX;
+    const CtaRef cr = resolve_cta(map);
+    const GridRef& gr = grids[cr.g];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const LevelDesc& lv = gr.lv[st->level];
+
+    const float* in;
+    long long in_row, in_cell;
+    int R, NC, r, rp, ntp;
+    const float* taps;
+    if (pass == 0) {  // along y: G -> H1 ([x][y][d])
+        in = gr.G; in_row = (long long)gr.W * gs; in_cell = gs;
+        R = gr.H; NC = gr.W * D;
+        r = lv.ry; rp = lv.rpy; ntp = lv.ntpy;
+        taps = gr.table + lv.off_ty;
+    } else {          // along x: H1 -> T ([y][x][d], cell stride ts)
+        in = gr.H1; in_row = (long long)gr.H * D; in_cell = D;
+        R = gr.W; NC = gr.H * D;
+        r = lv.rx; rp = lv.rpx; ntp = lv.ntpx;
+        taps = gr.table + lv.off_tx;
+    }
+    const int ncol = (NC + kDirCols - 1) / kDirCols;
+    const int c0 = (cr.local % ncol) * kDirCols;
+    const int t0 = (cr.local / ncol) * kDirTY;
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const unsigned dinv = D > 1 ? (unsigned)((0x100000000ull + (unsigned)D - 1) / (unsigned)D) : 0u;
+    long long inoff[2];
+    int ccell[2], cch[2];
+    bool ok[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int c = c0 + 32 * k + lane;
+        ok[k] = c < NC;
+        ccell[k] = D > 1 ? (int)__umulhi((unsigned)c, dinv) : c;
+        cch[k] = c - ccell[k] * D;
+        inoff[k] = ok[k] ? (long long)ccell[k] * in_cell + cch[k] : 0;
+    }
+    const int ylo = t0 + q * X;
+    if (ylo < R) {
+        // the warp's step range: non-zero taps that reach an in-range row
+        const int yhi = min(ylo + X, R) - 1;
+        int wlo = max(rp - r, rp - yhi);
+        wlo = wlo / X * X;
+        const int whi = min(rp + r, rp + R - 1 - ylo);
+        const int wend = min(ntp, (whi + X) / X * X);
+        float2 acc[X];
+#pragma unroll
+        for (int i = 0; i < X; ++i) acc[i] = make_float2(0.0f, 0.0f);
+        const float2* tp = reinterpret_cast<const float2*>(taps) + wlo;
+        const int base = ylo - rp + wlo;
+        const int nb = (wend - wlo) / X;
+        if (nb == 1) {
+            dir_chains<1>(in, in_row, inoff, ok, R, base, tp, acc);
+        } else if (nb == 2) {
+            dir_chains<2>(in, in_row, inoff, ok, R, base, tp, acc);
+        } else if (nb == 3) {
+            dir_chains<3>(in, in_row, inoff, ok, R, base, tp, acc);
+        } else {
+            for (int b = 0; b < nb; ++b) dir_chains<1>(in, in_row, inoff, ok, R, base + X * b, tp + X * b, acc);
+        }
+        float* out;
+        long long out_row, out_cell;
+        const float* norm;
+        if (pass == 0) {
+            out = gr.H1; out_row = D; out_cell = (long long)gr.H * D;
+            norm = gr.table + lv.off_ny;
+        } else {
+            out = gr.T; out_row = ts; out_cell = (long long)gr.W * ts;
+            norm = gr.table + lv.off_nx;
+        }
+        const float* rnorm = norm + ((R + 3) & ~3);  // RN(1/n) per position
+        long long ooff[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) ooff[k] = ok[k] ? (long long)ccell[k] * out_cell + cch[k] : 0;
+#pragma unroll
+        for (int i = 0; i < X; ++i) {
+            const int y = ylo + i;
+            if (y < R) {
+                const float nrm = norm[y];
+                const float rcp = rnorm[y];
+                float* orow = out + (long long)y * out_row;
+                const float v[2] = {acc[i].x, acc[i].y};
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (ok[k]) orow[ooff[k]] = div_rn(v[k], nrm, rcp);
+            }
+        }
+    }
+    if (pass == 0) write_group_table(gr, lv, st, cr.local, cr.count, kDirThreads);
+}
+
 int fir_ctas(int rows, int cols, int variant) {
-    const int ty = variant == kFirSmallRadius ? FirSmall::TY
-                   : variant == kFirMediumRadius ? FirMedium::TY : FirLarge::TY;
+    if (variant == kFirSmallRadius) return ((cols + kDirCols - 1) / kDirCols) * ((rows + kDirTY - 1) / kDirTY);
+    const int ty = variant == kFirMediumRadius ? FirMedium::TY : FirLarge::TY;
     return ((cols + kFirCols - 1) / kFirCols) * ((rows + ty - 1) / ty);
 }
 
@@ -300,8 +431,6 @@ static void fir_opt_in() {
                          (int)fir_smem<FirLarge>());
     cudaFuncSetAttribute(fir_kernel<FirMedium>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fir_smem<FirMedium>());
-    cudaFuncSetAttribute(fir_kernel<FirSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fir_smem<FirSmall>());
     done[dev] = true;
 }
 
@@ -312,8 +441,8 @@ void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int
     if (ctas <= 0) return;
     fir_opt_in();
     if (variant == kFirSmallRadius)
-        fir_kernel<FirSmall><<<ctas, FirSmall::THREADS, fir_smem<FirSmall>(), s>>>(
-            pass, grids, map, D, grid_stride(D), target_stride(D));
+        fir_direct_kernel<<<ctas, kDirThreads, 0, s>>>(pass, grids, map, D, grid_stride(D),
+                                                        target_stride(D));
     else if (variant == kFirMediumRadius)
         fir_kernel<FirMedium><<<ctas, FirMedium::THREADS, fir_smem<FirMedium>(), s>>>(
             pass, grids, map, D, grid_stride(D), target_stride(D));

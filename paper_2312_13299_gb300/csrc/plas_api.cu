@@ -84,14 +84,16 @@ int count_levels(const plas_schedule& s, int H, int W) {
 }
 
 // Taps of one pass: pairs (k_j, k_j) for j = -rr..rr at pair index rp + j,
-// zero pairs before (rp - rr of them) and after (up to ntp pairs).
+// with rp = rr (the first tap at step 0) and zero pairs after, up to ntp, a
+// whole number of 8-step blocks.  (Any rp >= rr gives the same FMA chains,
+// since zero taps leave them unchanged; rp = rr needs the fewest blocks.)
 static void padded_tap_pairs(int r, int rcap, double sigma, int* rr_out, int* rp, int* ntp,
                              std::vector<float>& out) {
     const int X = kFirX;
     const int rr = std::min(r, rcap);
     *rr_out = rr;
-    *rp = (rr + X - 1) / X * X;
-    *ntp = (*rp + rr + 1 + X - 1) / X * X;
+    *rp = rr;
+    *ntp = (2 * rr + 1 + X - 1) / X * X;
     out.assign((size_t)2 * *ntp, 0.0f);
     for (int j = -rr; j <= rr; ++j) {
         double q = (double)j * (double)j;

@@ -71,7 +71,8 @@ size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 // What a sort of this shape on the current device uses: the installed entry
 // for (D, H, W), else the entry with the same D and the nearest cell count,
 // else the defaults.
-constexpr int kDefaultSmallBelow = 1;
+constexpr int kDirectTuneMaxR = 32;  // the tuner times the direct FIR kernel up to this radius
+constexpr int kDefaultSmallBelow = 8;
 constexpr int kDefaultMediumBelow = 96;
 constexpr int kDefaultAssignPerSm = 8;
 struct Tuning {

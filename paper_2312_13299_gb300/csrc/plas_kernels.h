@@ -27,9 +27,9 @@ struct Weights {
     float w[kMaxD];
 };
 
-// Per-level blur geometry.  Taps are stored as duplicated pairs (k, k), padded
-// on the left to a multiple of kFirX ('rp' zero taps before tap -r) and on the
-// right to 'ntp' entries.  The border norms of an axis of length len follow,
+// Per-level blur geometry.  Taps are stored as duplicated pairs (k, k): tap j
+// (-r <= j <= r) at pair index rp + j (rp = r, so tap -r is step 0), then
+// zero pairs up to 'ntp' entries, a multiple of kFirX.  The border norms of an axis of length len follow,
 // then (at offset round_up(len, 4)) their reciprocals RN(1/n).
 struct LevelDesc {
     double phi;

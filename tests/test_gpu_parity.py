@@ -196,8 +196,8 @@ def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
     t = plas.autotune(H, W, D)
     assert t["radius"][0] == 1 and len(t["fir_small_us"]) == len(t["radius"])
     assert len(t["fir_medium_us"]) == len(t["radius"])
-    assert all(v > 0 for v in t["fir_small_us"] + t["fir_medium_us"] + t["fir_large_us"]
-               + t["assign_us"])
+    assert all(v > 0 for v in t["fir_medium_us"] + t["fir_large_us"] + t["assign_us"])
+    assert all((v > 0) == (r <= 32) for v, r in zip(t["fir_small_us"], t["radius"]))
     assert t["fir_small_below"] <= t["fir_medium_below"]
     assert t["assign_ctas_per_sm"] in t["assign_per_sm"]
     rng = np.random.default_rng(11)
