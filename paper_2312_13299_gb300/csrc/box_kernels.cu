@@ -390,6 +390,152 @@ __global__ void __launch_bounds__(kRowThreads) box_rows_kernel(const GridRef* __
     write_group_table(gr, lv, st, blockIdx.x, gridDim.x, kRowThreads);
 }
 
+// One CTA per row with all channel pairs (rows whose prefix fits in shared
+// memory, D <= 16): thread t owns cells [t*cpt, (t+1)*cpt).  It loads the
+// cells' P lines (16 B per pair, contiguous per cell, so a warp reads whole
+// lines), forms V = P(yb) - P(ya) and its running prefix per channel, the
+// CTA scans the thread totals (warp shuffles, then one warp over the warp
+// totals), and the prefix R goes to shared memory.  Each cell then reads
+// R(min(x+r, W-1)) - R(x-r-1) for every pair and writes its whole target
+// line, pad channels included, as 16-byte stores.
+constexpr int kRowCtaThreads = 512;
+constexpr int kRowCtaMaxBytes = 200 * 1024;  // the row prefix of every pair
+
+template <int PAIRS>
+__global__ void __launch_bounds__(kRowCtaThreads, 1) box_rowcta_kernel(const GridRef* __restrict__ grids, int D,
+                                                                       int ts) {
+    extern __shared__ longlong2 R[];  // W x PAIRS
+    __shared__ long long wtot[kRowCtaThreads / 32][2 * PAIRS];
+    const GridRef& gr = grids[0];
+    const DevState* st = gr.st;
+    if (sweep_idle(st)) return;
+    const LevelDesc& lv = gr.lv[st->level];
+    const int H = gr.H, W = gr.W, r = lv.r;
+    const int y = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int yb = min(y + r, H - 1), ya = y - r - 1;
+    const longlong2* P = reinterpret_cast<const longlong2*>(gr.sat);
+    const longlong2* pb = P + (long long)yb * W * PAIRS;
+    const longlong2* pa = P + (long long)max(ya, 0) * W * PAIRS;
+    const int cpt = (W + kRowCtaThreads - 1) / kRowCtaThreads;
+    const int c0 = min(t * cpt, W), c1 = min(c0 + cpt, W);
+    long long s[2 * PAIRS];
+#pragma unroll
+    for (int c = 0; c < 2 * PAIRS; ++c) s[c] = 0;
+    for (int x = c0; x < c1; ++x) {
+        longlong2 v[PAIRS];
+#pragma unroll
+        for (int j = 0; j < PAIRS; ++j) v[j] = __ldg(pb + (long long)x * PAIRS + j);
+        if (ya >= 0) {
+#pragma unroll
+            for (int j = 0; j < PAIRS; ++j) {
+                const longlong2 a = __ldg(pa + (long long)x * PAIRS + j);
+                v[j].x -= a.x;
+                v[j].y -= a.y;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PAIRS; ++j) {
+            s[2 * j] += v[j].x;
+            s[2 * j + 1] += v[j].y;
+            R[(long long)x * PAIRS + j] = make_longlong2(s[2 * j], s[2 * j + 1]);
+        }
+    }
+    // exclusive prefix of the thread totals: within the warp, then over warps
+    long long e[2 * PAIRS];
+#pragma unroll
+    for (int c = 0; c < 2 * PAIRS; ++c) {
+        long long v = s[c];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = shfl_up64(v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wtot[warp][c] = v;
+        e[c] = v - s[c];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = kRowCtaThreads / 32;
+#pragma unroll
+        for (int c = 0; c < 2 * PAIRS; ++c) {
+            const long long w0 = lane < NW ? wtot[lane][c] : 0LL;
+            long long v = w0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = shfl_up64(v, o);
+                if (lane >= o) v += u;
+            }
+            if (lane < NW) wtot[lane][c] = v - w0;  // exclusive over the warps
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2 * PAIRS; ++c) e[c] += wtot[warp][c];
+    for (int x = c0; x < c1; ++x) {
+#pragma unroll
+        for (int j = 0; j < PAIRS; ++j) {
+            longlong2 v = R[(long long)x * PAIRS + j];
+            v.x += e[2 * j];
+            v.y += e[2 * j + 1];
+            R[(long long)x * PAIRS + j] = v;
+        }
+    }
+    __syncthreads();
+    const int ny = yb - max(y - r, 0) + 1;
+    const float inv_scale = pow2f(-st->box_exp);
+    float* out = gr.T + (long long)y * W * ts;
+    for (int x = t; x < W; x += kRowCtaThreads) {
+        const int xb = min(x + r, W - 1), xa = x - r - 1;
+        const float n = (float)(ny * (xb - max(x - r, 0) + 1));
+        // the target line: TSP = round_up(D, 4) floats for D = 2 PAIRS - 1 or
+        // 2 PAIRS (ts == TSP, checked by the launcher)
+        constexpr int TSP = (2 * PAIRS + 3) & ~3;
+        float v[TSP];
+#pragma unroll
+        for (int c = 0; c < TSP; ++c) v[c] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PAIRS; ++j) {
+            longlong2 S = R[(long long)xb * PAIRS + j];
+            if (xa >= 0) {
+                const longlong2 a = R[(long long)xa * PAIRS + j];
+                S.x -= a.x;
+                S.y -= a.y;
+            }
+            v[2 * j] = __fmul_rn(__fdiv_rn(__ll2float_rn(S.x), n), inv_scale);
+            if (2 * j + 1 < D) v[2 * j + 1] = __fmul_rn(__fdiv_rn(__ll2float_rn(S.y), n), inv_scale);
+        }
+        float4* o = reinterpret_cast<float4*>(out + (long long)x * TSP);
+#pragma unroll
+        for (int k = 0; k < TSP / 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    write_group_table(gr, lv, st, blockIdx.x, gridDim.x, kRowCtaThreads);
+}
+
+template <int PAIRS>
+void launch_rowcta_t(const GridRef* grid, int H, int W, int D, cudaStream_t s) {
+    const size_t smem = sizeof(longlong2) * (size_t)W * PAIRS;
+    box_rowcta_kernel<PAIRS><<<(unsigned)H, kRowCtaThreads, smem, s>>>(grid, D, target_stride(D));
+}
+
+// true if a row-per-CTA launch was made (D <= 16 and the row prefix fits)
+bool launch_rowcta(const GridRef* grid, int H, int W, int D, cudaStream_t s) {
+    const int pairs = sat_channels(D) / 2;
+    if (pairs > 8 || (size_t)W * pairs * sizeof(longlong2) > (size_t)kRowCtaMaxBytes) return false;
+    if (target_stride(D) != ((2 * pairs + 3) & ~3)) return false;  // holds for every D
+    switch (pairs) {
+        case 1: launch_rowcta_t<1>(grid, H, W, D, s); break;
+        case 2: launch_rowcta_t<2>(grid, H, W, D, s); break;
+        case 3: launch_rowcta_t<3>(grid, H, W, D, s); break;
+        case 4: launch_rowcta_t<4>(grid, H, W, D, s); break;
+        case 5: launch_rowcta_t<5>(grid, H, W, D, s); break;
+        case 6: launch_rowcta_t<6>(grid, H, W, D, s); break;
+        case 7: launch_rowcta_t<7>(grid, H, W, D, s); break;
+        default: launch_rowcta_t<8>(grid, H, W, D, s); break;
+    }
+    return true;
+}
+
 template <int D>
 void launch_rowscan_t(const GridRef* grid, int H, cudaStream_t s) {
     box_rowscan_kernel<D><<<(unsigned)H, kScanThreads, 0, s>>>(grid);
@@ -430,6 +576,14 @@ void prepare_box_launches() {
     if (dev < 0 || dev >= 64 || done[dev]) return;
     cudaFuncSetAttribute(box_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(longlong2) * kRowsMaxW));
+    cudaFuncSetAttribute(box_rowcta_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
+    cudaFuncSetAttribute(box_rowcta_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowCtaMaxBytes);
     done[dev] = true;
 }
 
@@ -438,8 +592,9 @@ void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cu
     if (W <= kRowsMaxW) {
         prepare_box_launches();
         box_colprefix_kernel<<<(unsigned)W, kScanThreads, 0, s>>>(grid, D, grid_stride(D));
-        box_rows_kernel<<<(unsigned)((long long)H * pairs), kRowThreads, sizeof(longlong2) * (size_t)W, s>>>(
-            grid, D, target_stride(D));
+        if (!launch_rowcta(grid, H, W, D, s))
+            box_rows_kernel<<<(unsigned)((long long)H * pairs), kRowThreads, sizeof(longlong2) * (size_t)W, s>>>(
+                grid, D, target_stride(D));
         return;
     }
     launch_rowscan(grid, H, D, s);                                          // one CTA per row
