@@ -398,6 +398,9 @@ int orc_scale_exp(const float* x, long N, int D, const float* w, int normalize)
 /*   T_out    optional H x W x D: the target of the last iteration           */
 /* Returns the number of iterations run in this call, or -1 on bad input.    */
 /* ------------------------------------------------------------------------- */
+void orc_box_target(const float* G, int gs, int H, int W, int D, int r, int s_exp, float* T);
+int orc_box_exp(const float* x, long N, int D, const float* w, int normalize);
+
 long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t seed,
                    const orc_schedule* sch, const int32_t* perm_in, int resume, orc_state* st,
                    int32_t* perm_out, long long* trace_S, int* trace_level, long long trace_cap,
