@@ -21,12 +21,14 @@ def _cuda(a):
                                                  (1, 300, 15, 40.0, True), (257, 1, 2, 70.0, True),
                                                  (33, 70, 64, 12.0, True), (45, 38, 16, 9.0, False),
                                                  (4, 6144, 3, 100.0, True), (3, 7000, 3, 5.0, True),
-                                                 (2, 9000, 14, 2000.0, True), (3, 2000, 14, 300.0, True)])
+                                                 (2, 9000, 14, 2000.0, True), (3, 2000, 14, 300.0, True),
+                                                 (5, 1500, 14, 200.0, True)])
 def test_box_target_bitexact(plas, orc, H, W, D, phi, normalize):
     """Ragged and degenerate shapes (single row or column, odd D, D = 64).
-    Every row evaluation: one CTA per row (D <= 16, row prefix <= 200 KB),
-    one CTA per row and channel pair (up to 6144 cells: D = 64, and
-    2000 x 14), and the three-launch summed-area path for wider rows."""
+    Every row evaluation: one CTA per row (D <= 16, row prefix <= 200 KB,
+    e.g. 5 x 1500 x 14), one CTA per row and channel pair (up to 6144 cells:
+    D = 64, and 2000 x 14), and the three-launch summed-area path for wider
+    rows."""
     rng = np.random.default_rng(H * W + D)
     x = (rng.standard_normal((H * W, D)) * 3).astype(np.float32)
     perm = rng.permutation(H * W).astype(np.int32)
