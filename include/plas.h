@@ -43,6 +43,8 @@ extern "C" {
 #define PLAS_ERR_NONFINITE (-5)   /* input holds NaN or +-Inf               */
 #define PLAS_ERR_BUDGET (-6)      /* batch does not fit its memory budget   */
 #define PLAS_ERR_INTERNAL (-7)    /* an internal consistency check failed   */
+#define PLAS_ERR_NOT_PERMUTATION (-8) /* plas_check_permutation: not a        */
+                                      /* bijection of [0, N)                  */
 
 /* ---------------------------------------------------------------------- */
 /* schedule of the sort (Sec. 3.1, "Sorting High Dimensional Gaussians")  */
@@ -222,6 +224,20 @@ int plas_sort(const float* x, int H, int W, int D, const float* weights,
  */
 int plas_select_rows(const float* src, long long n_src, int C, const int32_t* idx,
                      long long n_out, float* dst, void* stream);
+/*
+ * plas_check_permutation -- checks that perm (device, N int32) is a
+ * permutation of [0, N), the one-to-one placement of Gaussians on grid cells
+ * that the sort produces (Sec. 3.1: every Gaussian lands on exactly one
+ * cell).  Returns PLAS_OK, or PLAS_ERR_NOT_PERMUTATION with *first_bad (host
+ * int, or NULL) = the smallest position whose value lies outside [0, N) or
+ * occurs more than once (a missing value implies such a position).
+ * *first_bad is -1 otherwise.  N = 0 is a valid, empty permutation.  Device
+ * work: two passes over perm with two bitmaps of ceil(N/32) words, allocated
+ * and freed on 'stream'; the call synchronises the stream.  Errors:
+ * PLAS_ERR_INVALID_ARG (N < 0 or N > 2^30, or perm NULL with N > 0), PLAS_ERR_OOM,
+ * PLAS_ERR_CUDA.
+ */
+int plas_check_permutation(const int32_t* perm, int N, int* first_bad, void* stream);
 int plas_gather_rows(const float* src, int N, int C, const int32_t* perm, float* dst,
                      void* stream);
 
@@ -448,19 +464,19 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
  *   shape on the current device would use (the defaults 8, 96 and 8 when
- *   nothing is installed).  A radius r takes the 32-row tiling when
+ *   nothing is installed).  A radius r takes the direct kernel when
  *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
  *   the 128-row one.  Thread-safe.
  */
 #define PLAS_TUNE_MAX_RADII 16
 #define PLAS_TUNE_ASSIGN_CANDIDATES 4
 typedef struct plas_tuning {
-    int fir_small_below;    /* the 32-row FIR tiling for radii below this      */
+    int fir_small_below;    /* the direct FIR kernel for radii below this      */
     int fir_medium_below;   /* else the 64-row tiling for radii below this     */
     int assign_ctas_per_sm; /* cap on assignment CTAs per SM, 1..16           */
     int n_radii;            /* radii measured by plas_autotune                */
     int radius[PLAS_TUNE_MAX_RADII];
-    float fir_small_us[PLAS_TUNE_MAX_RADII];  /* both passes, 32-row direct;
+    float fir_small_us[PLAS_TUNE_MAX_RADII];  /* both passes, direct kernel;
                                                  -1: not timed (r > 32)       */
     float fir_medium_us[PLAS_TUNE_MAX_RADII]; /* both passes, 64-row tiling   */
     float fir_large_us[PLAS_TUNE_MAX_RADII];  /* both passes, 128-row tiling  */

@@ -27,7 +27,7 @@ from ._lib import check, load
 
 __all__ = ["Schedule", "SortResult", "sort", "batch_sort", "Server", "gather_rows", "target",
            "group_permutation", "philox", "grid_metrics", "smooth_loss", "SmoothLoss",
-           "num_levels", "sort_workspace_bytes", "load"]
+           "num_levels", "sort_workspace_bytes", "check_permutation", "load"]
 
 
 @dataclass
@@ -139,13 +139,15 @@ def sort(x: torch.Tensor, H: int, W: int, weights=None, carried: Optional[torch.
          seed: int = 0, schedule: Optional[Schedule] = None,
          perm_init: Optional[torch.Tensor] = None, state=None, want_sorted: bool = False,
          want_stats: bool = False, trace_cap: int = 0,
-         workspace: Optional[torch.Tensor] = None) -> SortResult:
+         workspace: Optional[torch.Tensor] = None, check_perm: bool = False) -> SortResult:
     """PLAS grid sort (Sec. 3.1): x [N, D] float32 on a CUDA device, N = H*W.
 
     Returns the permutation (perm[p] = row of x placed at grid cell p), the
     carried attributes in grid order, optionally x in grid order, the final
     schedule state (resumable together with the permutation), statistics and
-    a per-iteration trace of the fixed-point residual sum."""
+    a per-iteration trace of the fixed-point residual sum.  check_perm=True
+    verifies on the device that perm is a bijection (plas_check_permutation)
+    and raises PlasError with status PLAS_ERR_NOT_PERMUTATION if not."""
     lib = load()
     x = _need_cuda(x, "x")
     if x.dim() != 2 or x.shape[0] != H * W:
@@ -185,6 +187,8 @@ def sort(x: torch.Tensor, H: int, W: int, weights=None, carried: Optional[torch.
                            ws_ptr, ws_bytes, ctypes.byref(stats) if stats is not None else None,
                            _stream(dev))
     check(rc, "plas_sort")
+    if check_perm and check_permutation(perm) >= 0:
+        raise _lib.PlasError(_lib.PLAS_ERR_NOT_PERMUTATION, "plas_sort")
     res = SortResult(perm=perm, carried=carried_out, sorted=sorted_out, state=st.as_dict(),
                      stats=_stats_to_dict(stats) if stats is not None else None)
     if tS is not None:
@@ -193,6 +197,23 @@ def sort(x: torch.Tensor, H: int, W: int, weights=None, carried: Optional[torch.
         res.trace_S = tS[it0:it1]
         res.trace_level = tL[it0:it1]
     return res
+
+
+def check_permutation(perm: torch.Tensor) -> int:
+    """Bijection check on the device (Sec. 3.1: the sort places every Gaussian
+    on exactly one cell).  perm: int32 CUDA tensor of N values.  Returns -1 if
+    perm is a permutation of [0, N), else the smallest position whose value is
+    out of range or occurs more than once."""
+    lib = load()
+    perm = _need_cuda(perm, "perm", torch.int32).reshape(-1)
+    first = ctypes.c_int(-1)
+    with torch.cuda.device(perm.device):
+        rc = lib.plas_check_permutation(perm.data_ptr() if perm.numel() else None, perm.numel(),
+                                        ctypes.byref(first), _stream(perm.device))
+    if rc == _lib.PLAS_ERR_NOT_PERMUTATION:
+        return first.value
+    check(rc, "plas_check_permutation")
+    return -1
 
 
 def batch_sort(jobs: Sequence[dict], weights=None, schedule: Optional[Schedule] = None,
@@ -269,7 +290,7 @@ def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
                fir_medium_below: Optional[int] = None) -> None:
     """Install launch shapes for (H, W, D) on the current device; with every
     argument None the entry is removed (defaults apply again).  A radius r
-    takes the 32-row FIR tiling when r < fir_small_below, else the 64-row one
+    takes the direct FIR kernel when r < fir_small_below, else the 64-row one
     when r < fir_medium_below, else the 128-row one."""
     if fir_small_below is None and assign_ctas_per_sm is None and fir_medium_below is None:
         check(load().plas_set_tuning(H, W, D, None), "plas_set_tuning")

@@ -23,6 +23,7 @@ PLAS_ERR_TIMEOUT = -4
 PLAS_ERR_NONFINITE = -5
 PLAS_ERR_BUDGET = -6
 PLAS_ERR_INTERNAL = -7
+PLAS_ERR_NOT_PERMUTATION = -8
 
 K_PREP, K_BLUR_ROWS, K_BLUR_COLS, K_GROUPS, K_ASSIGN, K_GATHER, K_COUNT = range(7)
 KERNEL_NAMES = ["prep", "blur_rows", "blur_cols", "groups", "assign", "gather"]
@@ -99,6 +100,7 @@ SIGNATURES = {
     "plas_philox": (c_int, [c_void_p, c_uint32, c_uint32, c_int, c_void_p, c_void_p]),
     "plas_grid_metrics": (c_int, [c_void_p, c_int, c_int, c_int, c_double, P(c_double),
                                   c_void_p]),
+    "plas_check_permutation": (c_int, [c_void_p, c_int, P(c_int), c_void_p]),
     "plas_smooth_loss_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
     "plas_smooth_loss_fwd": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_int, c_void_p,
                                      c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -303,6 +303,7 @@ const char* plas_status_string(int status) {
         case PLAS_ERR_NONFINITE: return "input holds NaN or Inf";
         case PLAS_ERR_BUDGET: return "request exceeds the memory budget";
         case PLAS_ERR_INTERNAL: return "internal error";
+        case PLAS_ERR_NOT_PERMUTATION: return "not a permutation";
         default: return "unknown status";
     }
 }
@@ -462,6 +463,44 @@ int plas_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32
     if (n < 0 || (n > 0 && (!ctr || !out))) return fail(PLAS_ERR_INVALID_ARG, "bad arguments");
     launch_philox(ctr, key0, key1, n, out, (cudaStream_t)stream);
     return check_launch("philox");
+}
+
+int plas_check_permutation(const int32_t* perm, int N, int* first_bad, void* stream) {
+    g_last_error.clear();
+    if (first_bad) *first_bad = -1;
+    if (N < 0 || N > (1 << 30) || (N > 0 && !perm))
+        return fail(PLAS_ERR_INVALID_ARG, "0 <= N <= 2^30 and a non-NULL perm required");
+    if (N == 0) return PLAS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t words = ((size_t)N + 31) / 32;
+    const size_t bytes = 16 + 2 * words * sizeof(uint32_t);
+    char* mem = nullptr;
+    if (cudaMallocAsync((void**)&mem, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PLAS_ERR_OOM, "allocation failed");
+    }
+    int* res = reinterpret_cast<int*>(mem);
+    uint32_t* seen = reinterpret_cast<uint32_t*>(mem + 16);
+    uint32_t* dup = seen + words;
+    const int init = 0x7fffffff;
+    int h = init;
+    int rc = PLAS_OK;
+    if (cudaMemsetAsync(seen, 0, 2 * words * sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemcpyAsync(res, &init, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = fail(PLAS_ERR_CUDA, "initialisation failed");
+    if (rc == PLAS_OK) {
+        launch_check_permutation(perm, N, seen, dup, res, num_sms(), st);
+        rc = check_launch("check_permutation");
+    }
+    if (rc == PLAS_OK && (cudaMemcpyAsync(&h, res, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                          cudaStreamSynchronize(st) != cudaSuccess))
+        rc = fail(PLAS_ERR_CUDA, "readback failed");
+    cudaFreeAsync(mem, st);
+    if (rc != PLAS_OK) return rc;
+    if (h == init) return PLAS_OK;
+    if (first_bad) *first_bad = h;
+    return fail(PLAS_ERR_NOT_PERMUTATION,
+                "position %d holds a value outside [0, %d) or one that occurs more than once", h, N);
 }
 
 int plas_grid_metrics(const float* grid, int H, int W, int D, double scale, double* out,

@@ -67,7 +67,7 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
                         char* base, bool sat = false);
 size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 
-// ---- launch-shape tuning (tune.cu) ---------------------------------------------------
+// ---- launch-shape tuning (plas_api.cu) ---------------------------------------------------
 // What a sort of this shape on the current device uses: the installed entry
 // for (D, H, W), else the entry with the same D and the nearest cell count,
 // else the defaults.
@@ -76,7 +76,7 @@ constexpr int kDefaultSmallBelow = 8;
 constexpr int kDefaultMediumBelow = 96;
 constexpr int kDefaultAssignPerSm = 8;
 struct Tuning {
-    int small_below = kDefaultSmallBelow;    // 32-row FIR tiling below this radius
+    int small_below = kDefaultSmallBelow;    // direct FIR kernel (no ring) below this radius
     int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row
     int assign_per_sm = kDefaultAssignPerSm;
 };

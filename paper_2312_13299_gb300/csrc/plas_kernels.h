@@ -136,6 +136,11 @@ void launch_box_target(const GridRef* grid, int H, int W, int D, int num_sms, cu
 
 // ---- outputs -----------------------------------------------------------------
 void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream_t s);
+// bijection check of perm over [0, N): res[0] (preset to INT_MAX) receives the
+// smallest position holding an out-of-range or repeated value; seen and dup
+// are zeroed bitmaps of ceil(N/32) words
+void launch_check_permutation(const int32_t* perm, int N, uint32_t* seen, uint32_t* dup, int* res,
+                              int num_sms, cudaStream_t s);
 // dst[p] = src[perm[p]] for p < N; src has Nsrc rows (< 0: N).  Entries of
 // perm outside [0, Nsrc) are not read; their rows are written as zeros.
 void launch_gather_rows(const float* src, long long N, int C, const int32_t* perm, float* dst,

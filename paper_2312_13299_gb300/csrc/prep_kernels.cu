@@ -267,6 +267,40 @@ void launch_extract_perm(const float* G, int N, int D, int32_t* perm, cudaStream
     extract_perm_kernel<<<ceil_div_u(N, 256), 256, 0, s>>>(G, N, grid_stride(D), D, perm);
 }
 
+// Bijection check of a permutation of [0, N) (the sort places every
+// Gaussian on exactly one cell, Sec. 3.1).  Pass 1 marks each in-range value
+// in 'seen' and, if it was marked already, in 'dup'; pass 2 takes the
+// smallest position whose value is out of range or marked in 'dup'.  Both
+// bitmaps hold ceil(N/32) words and start at zero; res[0] starts at INT_MAX.
+// A value missing from perm implies an out-of-range or repeated value
+// elsewhere, so res[0] == INT_MAX exactly when perm is a permutation.
+__global__ void check_perm_mark_kernel(const int32_t* __restrict__ perm, int N, uint32_t* seen,
+                                       uint32_t* dup) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int v = perm[p];
+        if (v < 0 || v >= N) continue;
+        const uint32_t bit = 1u << (v & 31);
+        if (atomicOr(&seen[v >> 5], bit) & bit) atomicOr(&dup[v >> 5], bit);
+    }
+}
+
+__global__ void check_perm_first_kernel(const int32_t* __restrict__ perm, int N,
+                                        const uint32_t* __restrict__ dup, int* res) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int v = perm[p];
+        const bool bad = v < 0 || v >= N || ((dup[v >> 5] >> (v & 31)) & 1u);
+        if (bad) atomicMin(res, p);
+    }
+}
+
+void launch_check_permutation(const int32_t* perm, int N, uint32_t* seen, uint32_t* dup, int* res,
+                              int num_sms, cudaStream_t s) {
+    if (N <= 0) return;
+    const unsigned blocks = std::min<unsigned>(ceil_div_u(N, 256), (unsigned)num_sms * 8u);
+    check_perm_mark_kernel<<<blocks, 256, 0, s>>>(perm, N, seen, dup);
+    check_perm_first_kernel<<<blocks, 256, 0, s>>>(perm, N, dup, res);
+}
+
 // dst[p, c] = src[perm[p], c]; consecutive threads write consecutive floats.
 __global__ void gather_rows_kernel(const float* __restrict__ src, long long N, long long Nsrc, int C,
                                    const int32_t* __restrict__ perm, float* __restrict__ dst) {
