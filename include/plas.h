@@ -523,6 +523,18 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out);
  *   PLAS_SERVE_SHORTEST_FIRST: least estimated work left first, same fill;
  *   PLAS_SERVE_ALL: every admitted grid in every sweep.
  *   PLAS_ERR_INVALID_ARG for an unknown policy.
+ * plas_server_cancel: withdraws a request that is queued or running.  A
+ *   queued request is removed at once; a running one leaves the sweeps at
+ *   the next plas_server_step, which releases its workspace (stream-ordered,
+ *   after the sweeps already enqueued on it).  A cancelled request is never
+ *   reported in done[]; its outputs and state_out are left as they are.  No
+ *   work enqueued after that step touches its buffers, but work enqueued
+ *   before it may still read x on the server's stream: release them
+ *   stream-ordered on that stream, or after synchronising it.
+ *   The other requests' results do not change.  PLAS_ERR_INVALID_ARG for a
+ *   ticket that is unknown, already finished (its outputs are enqueued or
+ *   reported) or already cancelled.  The paper has no counterpart; it is a
+ *   serving control.
  * plas_server_status: queued and admitted requests, device bytes in use.
  * plas_server_destroy: waits for the stream and frees everything; requests
  *   still queued or running are abandoned (their outputs are undefined).
@@ -534,6 +546,7 @@ int plas_server_create(int D, const float* weights, const plas_schedule* sched,
 int plas_server_set_policy(plas_server* srv, int policy);
 int plas_server_submit(plas_server* srv, const plas_job* job, long long* ticket);
 int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap, int* n_done);
+int plas_server_cancel(plas_server* srv, long long ticket);
 int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use);
 int plas_server_destroy(plas_server* srv);
 

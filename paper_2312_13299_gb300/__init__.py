@@ -336,6 +336,8 @@ class Server:
         check(rc, "plas_server_create")
         self._h = h
         self._live = {}
+        self._cancelled = []  # (step number, tensors) kept until that step's work has run
+        self._steps = 0
         if policy not in self.POLICIES:
             self.close()
             raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
@@ -376,11 +378,22 @@ class Server:
         with torch.cuda.device(self.device):
             rc = self._lib.plas_server_step(self._h, sweeps, done, cap, ctypes.byref(n))
         check(rc, "plas_server_step")
+        self._steps += 1
+        self._cancelled = [c for c in self._cancelled if c[0] + 2 > self._steps]
         out = []
         for i in range(n.value):
             x, car, perm, cout, st = self._live.pop(done[i])
             out.append((done[i], SortResult(perm=perm, carried=cout, state=st.as_dict())))
         return out
+
+    def cancel(self, ticket: int) -> None:
+        """Withdraw a queued or running request (plas_server_cancel); it is
+        never reported by step().  Raises PlasError for a ticket that is
+        unknown, finished or already cancelled."""
+        check(self._lib.plas_server_cancel(self._h, ticket), "plas_server_cancel")
+        # the request's tensors stay referenced until work enqueued before
+        # the cancellation has run
+        self._cancelled.append((self._steps, self._live.pop(ticket)))
 
     def status(self):
         q, a, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
@@ -393,6 +406,7 @@ class Server:
             self._lib.plas_server_destroy(self._h)
             self._h = None
             self._live.clear()
+            self._cancelled.clear()
 
     def __del__(self):
         try:

@@ -132,6 +132,7 @@ SIGNATURES = {
     "plas_server_submit": (c_int, [c_void_p, P(plas_job), P(c_ll)]),
     "plas_server_step": (c_int, [c_void_p, c_int, P(c_ll), c_int, P(c_int)]),
     "plas_server_status": (c_int, [c_void_p, P(c_int), P(c_int), P(c_size_t)]),
+    "plas_server_cancel": (c_int, [c_void_p, c_ll]),
     "plas_server_destroy": (c_int, [c_void_p]),
     "plas_status_string": (ctypes.c_char_p, [c_int]),
     "plas_last_error": (ctypes.c_char_p, []),

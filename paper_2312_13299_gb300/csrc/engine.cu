@@ -57,6 +57,7 @@ struct Slot {
     int ctas[kClsCount] = {0, 0, 0};
     Tuning tune;  // FIR tiling choice (one-grid sweeps)
     bool active = false;
+    bool cancel = false;  // served request cancelled while admitted
     DevState last{};
     long long last_it = -1;
     int stuck = 0;
@@ -259,6 +260,15 @@ class Engine {
             }
         }
         return PLAS_OK;
+    }
+
+    // Take a grid out of the sweeps without outputs (a cancelled request).
+    // Sweeps already enqueued still run on its workspace; the caller frees
+    // that memory stream-ordered after them.
+    void drop(Slot* sl) {
+        sl->active = false;
+        active_.erase(std::remove(active_.begin(), active_.end(), sl), active_.end());
+        dirty_ = true;
     }
 
     // Enqueue the outputs of a finished grid and take it out of the sweeps.
@@ -1108,6 +1118,22 @@ extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, i
     *n_done = 0;
     srv->step_no += 1;
     Engine& eng = *srv->eng;
+    // cancelled requests leave the sweeps; their memory is released after
+    // the work already queued on them, and their host records are kept while
+    // a read-back in flight can name them
+    for (size_t i = 0; i < srv->running.size();) {
+        Slot* sl = srv->running[i].get();
+        if (!sl->cancel) {
+            ++i;
+            continue;
+        }
+        eng.drop(sl);
+        cudaFreeAsync(sl->mem, srv->st);
+        sl->mem = nullptr;
+        srv->in_use -= sl->bytes;
+        srv->graveyard.emplace_back(srv->step_no, std::move(srv->running[i]));
+        srv->running.erase(srv->running.begin() + i);
+    }
     // admission: FIFO, while the next request fits the budget
     while (!srv->queue.empty()) {
         Slot* sl = srv->queue.front().get();
@@ -1191,6 +1217,24 @@ extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, i
     srv->completed.erase(srv->completed.begin(), srv->completed.begin() + n);
     *n_done = n;
     return PLAS_OK;
+}
+
+extern "C" int plas_server_cancel(plas_server* srv, long long ticket) {
+    set_last_error("");
+    if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
+    for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it)
+        if ((*it)->job.ticket == ticket) {
+            srv->queue.erase(it);
+            return PLAS_OK;
+        }
+    for (auto& p : srv->running)
+        if (p->job.ticket == ticket) {
+            if (!p->active || p->cancel)
+                return fail(PLAS_ERR_INVALID_ARG, "request %lld has finished or was cancelled", ticket);
+            p->cancel = true;
+            return PLAS_OK;
+        }
+    return fail(PLAS_ERR_INVALID_ARG, "request %lld is not queued or running", ticket);
 }
 
 extern "C" int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use) {

@@ -106,3 +106,61 @@ def test_server_rejects_request_over_budget(plas):
         srv.submit(x, 64, 64)
     assert "budget" in str(e.value)
     srv.close()
+
+
+def test_server_cancel_queued_and_running(plas):
+    """A request cancelled while queued and one cancelled while running are
+    never reported; the others give exactly their results alone, and the
+    server ends with nothing queued, admitted or allocated.  Unknown,
+    finished and repeated cancellations are rejected."""
+    reqs = _requests(seed0=30)[:4]
+    srv = plas.Server(14, policy="all")
+    t = [srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"]) for r in reqs]
+    srv.cancel(t[2])  # still queued: nothing is admitted before the first step
+    with pytest.raises(RuntimeError):
+        srv.cancel(t[2])
+    results = dict(srv.step(sweeps=2))
+    assert srv.status()[1] == 3
+    srv.cancel(t[1])  # admitted and running
+    steps = 0
+    while len(results) < 2:
+        results.update(srv.step(sweeps=8))
+        steps += 1
+        assert steps < 100000
+    for _ in range(3):
+        results.update(srv.step(sweeps=8))
+    assert sorted(results) == sorted([t[0], t[3]])
+    for i in (0, 3):
+        _same(results[t[i]], _alone(plas, reqs[i]))
+    assert srv.status() == (0, 0, 0)
+    with pytest.raises(RuntimeError):
+        srv.cancel(t[0])  # finished
+    with pytest.raises(RuntimeError):
+        srv.cancel(12345)  # unknown
+    srv.close()
+
+
+def test_server_cancel_frees_budget_for_the_next_request(plas):
+    """With a budget for one request at a time, cancelling the running
+    request admits the queued one at the next step, and that one completes
+    with its result alone."""
+    reqs = _requests(seed0=40)
+    big, small = reqs[5], reqs[0]  # 128 x 128 and 48 x 48
+    need = plas.sort_workspace_bytes(big["H"], big["W"], 14)
+    srv = plas.Server(14, mem_budget=need + 4096)
+    tb = srv.submit(big["x"], big["H"], big["W"], big["carried"], big["seed"])
+    ts = srv.submit(small["x"], small["H"], small["W"], small["carried"], small["seed"])
+    assert srv.step(sweeps=2) == []
+    q, a, mem = srv.status()
+    assert (q, a) == (1, 1) and mem > 0
+    srv.cancel(tb)
+    results = {}
+    steps = 0
+    while ts not in results:
+        results.update(srv.step(sweeps=8))
+        steps += 1
+        assert steps < 100000
+    assert list(results) == [ts]
+    _same(results[ts], _alone(plas, small))
+    assert srv.status() == (0, 0, 0)
+    srv.close()
