@@ -76,16 +76,17 @@ def test_target_bitexact_wide_magnitudes(plas, orc, phi):
 
 
 # tuning that forces one FIR tiling at every radius: (small_below, medium_below)
-_TILINGS = {"32-row": (10 ** 6, 10 ** 6), "64-row": (0, 10 ** 6), "128-row": (0, 0)}
+_TILINGS = {"direct": (10 ** 6, 10 ** 6), "64-row": (0, 10 ** 6), "128-row": (0, 0)}
 
 
 @pytest.mark.parametrize("tiling", sorted(_TILINGS))
 @pytest.mark.parametrize("H,W,D,phi", [(200, 136, 14, 60.0), (131, 77, 5, 30.0), (96, 160, 3, 6.0),
                                        (1, 300, 14, 40.0), (257, 1, 2, 70.0), (68, 52, 64, 20.0)])
 def test_target_bitexact_every_tiling(plas, orc, tiling, H, W, D, phi):
-    """Each FIR tiling (32, 64 or 128 rows per CTA) gives the oracle's target
-    bit for bit, on ragged grids whose sides and column counts span several
-    tiles with partial ones at the end, and on single-row/column grids."""
+    """Each FIR tiling (the direct kernel, or the ring kernel with 64 or 128
+    rows per CTA) gives the oracle's target bit for bit, on ragged grids
+    whose sides and column counts span several tiles with partial ones at the
+    end, and on single-row/column grids."""
     rng = np.random.default_rng(H * 7 + W * 3 + D)
     x = rng.random((H * W, D), dtype=np.float32)
     perm = rng.permutation(H * W).astype(np.int32)
@@ -189,7 +190,7 @@ def test_launch_modes_give_identical_results(plas, orc):
 
 def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
     """The tuner measures the three FIR tilings and four assignment grid sizes;
-    any installed choice (always 128-row, always 64-row, always 32-row, a
+    any installed choice (always 128-row, always 64-row, always direct, a
     mix by radius, 1 or 16 assignment CTAs per SM) gives the oracle's
     permutation and schedule trace."""
     H, W, D = 72, 56, 5
