@@ -33,30 +33,61 @@ __device__ __forceinline__ uint32_t opacity_key(float v) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-__global__ void activate_kernel(const float* __restrict__ raw, long long n, int stride,
-                                float* __restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float* r = raw + i * stride;
-        float* o = out + i * 14;
+// A CTA activates blocks of kActRows rows.  The 14 leading floats of each
+// raw row are read as contiguous 56-byte runs (consecutive threads take
+// consecutive floats of a row, then of the next row), one thread per row
+// activates them in shared memory, and the block's output, kActRows x 14
+// contiguous floats, is written back with consecutive threads on consecutive
+// floats.  The tile pads rows to 15 floats, so the per-row accesses of the
+// middle step fall in distinct banks.
+constexpr int kActRows = 256, kActPad = 15;
+
+__device__ __forceinline__ void activate_row(const float* r, float* o) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {  // coordinates: sign(v) (exp(|v|) - 1), via expm1
-            const float v = r[k];
-            const float m = expm1f(fabsf(v));
-            o[k] = v < 0.0f ? -m : m;
+    for (int k = 0; k < 3; ++k) {  // coordinates: sign(v) (exp(|v|) - 1), via expm1
+        const float v = r[k];
+        const float m = expm1f(fabsf(v));
+        o[k] = v < 0.0f ? -m : m;
+    }
+#pragma unroll
+    for (int k = 3; k < 6; ++k) o[k] = expf(r[k]);  // scale
+    const float q0 = r[6], q1 = r[7], q2 = r[8], q3 = r[9];
+    const float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)),
+                                                    __fmul_rn(q2, q2)),
+                                          __fmul_rn(q3, q3)));
+    const float qs[4] = {q0, q1, q2, q3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[6 + k] = nn > 0.0f ? __fdiv_rn(qs[k], nn) : 0.0f;
+    o[10] = __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-r[10])));  // opacity
+#pragma unroll
+    for (int k = 11; k < 14; ++k) o[k] = r[k];  // DC colour
+}
+
+__global__ void __launch_bounds__(kActRows) activate_kernel(const float* __restrict__ raw, long long n,
+                                                            int stride, float* __restrict__ out) {
+    __shared__ float tile[kActRows * kActPad];
+    for (long long base = (long long)blockIdx.x * kActRows; base < n;
+         base += (long long)gridDim.x * kActRows) {
+        const int rows = (int)min((long long)kActRows, n - base);
+        for (int e = threadIdx.x; e < rows * 14; e += kActRows) {
+            const int r = e / 14, k = e - r * 14;
+            tile[r * kActPad + k] = __ldg(raw + (base + r) * stride + k);
         }
+        __syncthreads();
+        if ((int)threadIdx.x < rows) {
+            float v[14];
+            float* t = tile + threadIdx.x * kActPad;
 #pragma unroll
-        for (int k = 3; k < 6; ++k) o[k] = expf(r[k]);  // scale
-        const float q0 = r[6], q1 = r[7], q2 = r[8], q3 = r[9];
-        const float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)),
-                                                        __fmul_rn(q2, q2)),
-                                              __fmul_rn(q3, q3)));
-        const float qs[4] = {q0, q1, q2, q3};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) o[6 + k] = nn > 0.0f ? __fdiv_rn(qs[k], nn) : 0.0f;
-        o[10] = __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-r[10])));  // opacity
-#pragma unroll
-        for (int k = 11; k < 14; ++k) o[k] = r[k];  // DC colour
+            for (int k = 0; k < 14; ++k) v[k] = t[k];
+            activate_row(v, t);
+        }
+        __syncthreads();
+        float* o = out + base * 14;
+        for (int e = threadIdx.x; e < rows * 14; e += kActRows) {
+            const int r = e / 14, k = e - r * 14;
+            o[e] = tile[r * kActPad + k];
+        }
+        __syncthreads();
     }
 }
 
@@ -278,8 +309,8 @@ extern "C" int plas_activate_3dgs(const float* raw, long long N, int stride, flo
     if (N < 0 || stride < 14) return fail(PLAS_ERR_INVALID_ARG, "N >= 0 and stride >= 14 required");
     if (N == 0) return PLAS_OK;
     if (!raw || !out) return fail(PLAS_ERR_INVALID_ARG, "raw and out are required");
-    const unsigned blocks = (unsigned)std::min<long long>((N + 255) / 256, (long long)num_sms() * 16);
-    activate_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(raw, N, stride, out);
+    const unsigned blocks = (unsigned)std::min<long long>((N + kActRows - 1) / kActRows, (long long)num_sms() * 8);
+    activate_kernel<<<blocks, kActRows, 0, (cudaStream_t)stream>>>(raw, N, stride, out);
     return check_launch("activate");
 }
 

@@ -37,6 +37,20 @@ def test_activation_close_to_fp64(plas, orc):
     assert np.all(np.abs(got - want) <= tol)
 
 
+@pytest.mark.parametrize("n,stride", [(1, 14), (255, 59), (257, 59), (100_003, 59), (4096, 15)])
+def test_activation_strided_rows_and_tails(plas, orc, n, stride):
+    """Rows of the 59-channel layout (only the first 14 are read), blocks of
+    256 rows cut by a ragged tail, and a single row: within a few ulp of the
+    FP64 oracle, and the extra columns never leak into the output."""
+    rng = np.random.default_rng(n + stride)
+    raw = rng.normal(0, 2, (n, stride)).astype(np.float32)
+    got = plas.activate_3dgs(torch.from_numpy(raw).cuda()).cpu().numpy()
+    want = orc.activate_3dgs(raw)
+    assert got.shape == (n, 14)
+    tol = 4 * np.spacing(np.abs(want).astype(np.float32)) + 1e-30
+    assert np.all(np.abs(got - want) <= tol)
+
+
 def test_prepare_then_sort_matches_oracle(plas, orc):
     rng = np.random.default_rng(5)
     raw = rng.normal(0, 1.5, (70 * 70 + 123, 14)).astype(np.float32)
