@@ -13,8 +13,10 @@ the target).
   arrangements for the target of that iteration (brute force in FP64); on a
   3x3 grid each of the two groups is brute-force optimal and the leftover cell
   stays.
-* Invariants over many iterations: the output is a bijection, and the summed
-  squared distance to the iteration's target never increases.
+* Invariants over many iterations: the output is a bijection, the summed
+  squared distance to the iteration's target never increases, and the
+  schedule's residual (the exact fixed-point sum of per-cell L2 distances)
+  equals numpy's FP64 sum within the rounding of its terms.
 """
 import itertools
 
@@ -124,6 +126,15 @@ def test_invariants_per_iteration(orc, H, W, D):
         assert np.array_equal(T, orc.target(x, H, W, perm, phis[lvl]).reshape(H * W, D))
         before, after = _sq(F[perm], T).sum(), _sq(F[new], T).sum()
         assert after <= before * (1 + 1e-9) + 1e-12
+        # the schedule's residual: the sum over all cells of the (non-squared)
+        # L2 distance to this iteration's target, each term rounded to a
+        # multiple of 2^-k; numpy in FP64 gives it independently (the FP32
+        # per-cell distances differ from it by a few ulp)
+        k = r["state"].scale_exp
+        e = np.sqrt(((F[new].astype(np.float64) - T.astype(np.float64)) ** 2).sum(axis=1))
+        S = float(r["trace_S"][0]) * 2.0 ** -k
+        assert abs(S - e.sum()) <= H * W * 2.0 ** -k + 4e-7 * e.sum()
+        assert r["state"].d_last == r["trace_S"][0] / (H * W * 2.0 ** k)
         perm, state = new, r["state"]
         if state.done:
             break
