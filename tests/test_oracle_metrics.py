@@ -32,3 +32,28 @@ def test_metrics_direct(orc):
     a = np.abs(np.concatenate([dh.ravel(), dv.ravel()])) * 2.0
     assert abs(nl2 - l2.mean()) < 1e-12
     assert abs(vad - a.var()) < 1e-10
+
+
+def test_3x3_sort_against_all_arrangements(orc):
+    """Brute force over all 9! = 362,880 arrangements of a 3x3 grid: the
+    optimal mean neighbour L2 E* is a lower bound for the sort's result (a
+    heuristic, so only the bound is asserted and the gap is printed), the
+    oracle's metric of the optimal arrangement equals E*, and the sort's
+    result lies below the mean over all arrangements."""
+    import itertools
+    x = np.random.default_rng(9).random((9, 3), dtype=np.float32)
+    F = orc.normalize(x).astype(np.float64)
+    perms = np.array(list(itertools.permutations(range(9))), dtype=np.int8)
+    G = F[perms].reshape(-1, 3, 3, 3)
+    dh = np.sqrt(((G[:, :, 1:] - G[:, :, :-1]) ** 2).sum(-1)).reshape(len(perms), -1)
+    dv = np.sqrt(((G[:, 1:] - G[:, :-1]) ** 2).sum(-1)).reshape(len(perms), -1)
+    E = np.concatenate([dh, dv], axis=1).mean(axis=1)
+    best = int(np.argmin(E))
+    e_star = float(E[best])
+    nl2_best = orc.metrics(F[perms[best]].reshape(3, 3, 3).astype(np.float32))[0]
+    assert abs(nl2_best - e_star) < 1e-6
+    r = orc.sort(x, 3, 3, seed=0)
+    e_plas = orc.metrics(F[r["perm"]].reshape(3, 3, 3).astype(np.float32))[0]
+    assert e_plas >= e_star - 1e-6
+    assert e_plas < float(E.mean())
+    print(f"3x3: E* = {e_star:.5f}, PLAS = {e_plas:.5f}, mean = {E.mean():.5f}")
