@@ -7,9 +7,9 @@ channels, 3DGS-shaped synthetic data, default schedule, inputs resident in HBM.
 A step is one full call of plas_sort (normalise, initial placement, every
 iteration of the shrinking-radius schedule, permutation + carried gather).
 
-  python bench.py [--steps K] [--warmup W] [--workload m1|cfg2|cfg3|cfg1|p0]
+  python bench.py [--steps K] [--warmup W] [--workload 3dgs-1024|3dgs-512|3dgs-1448|rgb-64|rgb-512]
   python bench.py --impl reference      # the CPU oracle on this host's cores
-  python bench.py --workload p0 --threshold-sweep   # VAD vs runtime over tol
+  python bench.py --workload rgb-512 --threshold-sweep   # VAD vs runtime over tol
 
 Under torchrun (N > 1) every rank sorts its own replica (different seed): the
 sort has no data-path exchange, so the job is N independent replicas and
@@ -32,16 +32,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "m1": dict(side=1024, D=14, C=45, kind="3dgs",
+    "3dgs-1024": dict(side=1024, D=14, C=45, kind="3dgs",
                desc="1024x1024 grid (N=1,048,576), 14 sort + 45 carried fp32 channels, "
                     "3DGS-shaped synthetic attributes, seed 0, default schedule"),
-    "cfg2": dict(side=512, D=14, C=45, kind="3dgs",
+    "3dgs-512": dict(side=512, D=14, C=45, kind="3dgs",
                  desc="512x512 grid (N=262,144), 14 sort + 45 carried fp32, 3DGS-shaped"),
-    "cfg3": dict(side=1448, D=14, C=45, kind="3dgs",
+    "3dgs-1448": dict(side=1448, D=14, C=45, kind="3dgs",
                  desc="1448x1448 grid (N=2,096,704), 14 sort + 45 carried fp32, 3DGS-shaped"),
-    "cfg1": dict(side=64, D=3, C=0, kind="rgb",
+    "rgb-64": dict(side=64, D=3, C=0, kind="rgb",
                  desc="64x64 grid (N=4096), 3 fp32 channels U[0,1)"),
-    "p0": dict(side=512, D=3, C=0, kind="rgb",
+    "rgb-512": dict(side=512, D=3, C=0, kind="rgb",
                desc="512x512 grid (N=262,144), 3 fp32 channels U[0,1) (paper's runtime test)"),
 }
 METRIC = "ms per 1M x 14-D grid sort"
@@ -53,7 +53,7 @@ FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
 NCU_TRAFFIC = {
     # profiles/launches_sort_1024x1024x14.md: DRAM read + write per launch of
     # the target pass along y, averaged over the 6504 such launches of one sort
-    ("blur_cols", "m1"): {"bytes_per_launch": 84955336, "src": "793aa4f395a0"},
+    ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 84955336, "src": "793aa4f395a0"},
 }
 
 
@@ -735,7 +735,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="plas", choices=["plas", "reference"])
-    ap.add_argument("--workload", default="m1", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="3dgs-1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--target", default="gaussian", choices=["gaussian", "box"],
                     help="low-pass target of the sort: the Gaussian (default) or the box variant")
@@ -754,7 +754,7 @@ def main():
                     help="smoothness-loss fwd/bwd benchmark on 1024x1024x59, own JSON line")
     ap.add_argument("--threshold-sweep", action="store_true",
                     help="VAD and runtime over the stall threshold, Gaussian and box target, "
-                         "own JSON line (use with --workload p0)")
+                         "own JSON line (use with --workload rgb-512)")
     ap.add_argument("--tols", default="1e-2,3e-3,1e-3,3e-4,1e-4,3e-5,1e-5",
                     help="with --threshold-sweep: the thresholds")
     ap.add_argument("--stages", action="store_true",

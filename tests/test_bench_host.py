@@ -29,7 +29,7 @@ def test_alu_bound_dominant_class(bench):
     peaks = {"hbm_gbs": 6784.5}
     # two steps: 30 ms of target passes at 40 TFLOP/s over 6 GB, 10 ms of assignment
     st = [_stats(15.0, 6e11, 3e9, 5.0, 1e10)] * 2
-    rl, per = bench.roofline(st, peaks, "measured", {"sm_max_mhz": 2070.0}, "m1")
+    rl, per = bench.roofline(st, peaks, "measured", {"sm_max_mhz": 2070.0}, "3dgs-1024")
     peak = 152 * 128 * 2 * 2070e6 / 1e12
     assert rl["kernel"] == "blur_cols" and rl["bound"] == "alu" and rl["unit"] == "TFLOP/s"
     assert rl["achieved"] == pytest.approx(40.0, abs=1e-3)
@@ -46,7 +46,7 @@ def test_hbm_bound_when_bytes_dominate(bench):
     peaks = {"hbm_gbs": 6000.0}
     # the assignment dominates the time and has no flops: bound by HBM
     st = [_stats(1.0, 1e9, 1e8, 9.0, 4.5e10)]
-    rl, _ = bench.roofline(st, peaks, "measured", None, "m1")
+    rl, _ = bench.roofline(st, peaks, "measured", None, "3dgs-1024")
     assert rl["kernel"] == "assign" and rl["bound"] == "hbm" and rl["unit"] == "GB/s"
     assert rl["achieved"] == pytest.approx(5000.0)
     assert rl["frac"] == pytest.approx(5000.0 / 6000.0, abs=1e-4)
@@ -55,15 +55,15 @@ def test_hbm_bound_when_bytes_dominate(bench):
 
 def test_traffic_only_for_the_measured_source(bench, monkeypatch):
     st = [_stats(15.0, 6e11, 3e9, 5.0, 1e10)]
-    key = ("blur_cols", "m1")
+    key = ("blur_cols", "3dgs-1024")
     rec = bench.NCU_TRAFFIC[key]
-    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "m1")
+    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "3dgs-1024")
     assert rl["traffic"] == (rec["bytes_per_launch"] if rec["src"] == bench._kernel_hash() else None)
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, {"bytes_per_launch": 123, "src": "not-this-source"})
-    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "m1")
+    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "3dgs-1024")
     assert rl["traffic"] is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, {"bytes_per_launch": 123, "src": bench._kernel_hash()})
-    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "m1")
+    rl, _ = bench.roofline(st, {"hbm_gbs": 6784.5}, "measured", None, "3dgs-1024")
     assert rl["traffic"] == 123
 
 
