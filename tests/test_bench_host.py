@@ -74,3 +74,30 @@ def test_pass_fmas_counts_in_range_taps(bench, length, r):
     assert bench.pass_fmas(length, r, other, D) == brute * other * D
     # the closed form the device counters use: len (2r + 1) - r (r + 1)
     assert brute == length * (2 * r + 1) - r * (r + 1)
+
+
+def test_clock_sampler_parsing(bench, tmp_path):
+    """The clocks entry of the report: the median SM clock over the samples
+    taken under load (utilisation >= 50 %), the maximum clock, and every
+    throttle reason seen active (nvidia-smi CSV rows, no header, no units)."""
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join([
+        "0, 345, 2070, 120.5, 0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 900.1, 100, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1380.0, 100, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.2, 99, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc, s.path = Done(), str(path)
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    assert not path.exists()
