@@ -47,14 +47,17 @@ WORKLOADS = {
 METRIC = "ms per 1M x 14-D grid sort"
 FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
 
-# Per-launch DRAM traffic of the dominant kernels from committed ncu
-# summaries (profiles/), keyed by the sha1 of the kernel source they were
-# taken on; a stale hash reports null.
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the dominant kernel class, averaged over every launch of that class in one
+# sort of the workload, from an ncu launch list of
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none --csv python bench.py --steps 1 --warmup 3 --no-cpu-baseline
+# keyed by the sha1 of the kernel source it was taken on: a stale hash
+# reports null.
 NCU_TRAFFIC = {
-    # profiles/launches_sort_1024x1024x14.md: DRAM read + write per launch of
-    # the target pass along y, averaged over the 6504 such launches of one sort
     ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 84955336, "src": "793aa4f395a0"},
 }
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def _env_int(name, default):
@@ -189,7 +192,43 @@ def roofline(stats_list, peaks, peaks_src, clocks, wl):
     return out, per_kernel
 
 
-def oracle_projection(x, wl, seed, level_counts, max_cpu_s=30.0):
+def oracle_level_counts(workload):
+    """Iterations per radius level of the complete oracle sort of this
+    workload (data seed 0, Philox seed 0, default schedule), from the fixture
+    that tests/golden/make_sort_goldens.py writes by running the oracle alone;
+    None when no such fixture exists."""
+    p = os.path.join(GOLDEN, f"oracle_sort_{workload}.json")
+    if not os.path.exists(p):
+        return None, p
+    with open(p) as f:
+        return json.load(f)["iterations_per_level"], p
+
+
+def cpu_baseline(x_np, workload, wl, max_cpu_s=20.0):
+    """The oracle's projected time per sort on this host's cores: all cores,
+    and one thread (sampled at middle and small radii only, so that the
+    bounded sample stays within seconds)."""
+    import oracle
+    counts, src = oracle_level_counts(workload)
+    if counts is None:
+        return {"value": None, "error": f"no oracle fixture {os.path.relpath(src, ROOT)}"}
+    oracle.build()
+    n_all = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(n_all)
+    ms, sample, cpu_s = oracle_projection(x_np, wl, 0, counts, max_cpu_s=max_cpu_s)
+    out = {"value": round(ms, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": sample, "cpu_seconds": round(cpu_s, 1), "projected": True,
+           "level_counts": f"oracle fixture {os.path.relpath(src, ROOT)}"}
+    oracle.set_num_threads(1)
+    ms1, sample1, cpu1 = oracle_projection(x_np, wl, 0, counts, max_cpu_s=max_cpu_s,
+                                           radii=(100.0, 10.0, 1.0))
+    oracle.set_num_threads(n_all)
+    out["one_thread"] = {"value": round(ms1, 1), "unit": "ms", "cores": 1, "sample": sample1,
+                         "cpu_seconds": round(cpu1, 1), "projected": True}
+    return out
+
+
+def oracle_projection(x, wl, seed, level_counts, max_cpu_s=30.0, radii=None):
     """Bounded CPU-oracle sample -> projected ms for the whole sort.
 
     The oracle runs one and two iterations resumed at the first iteration of a
@@ -198,14 +237,14 @@ def oracle_projection(x, wl, seed, level_counts, max_cpu_s=30.0):
     values, so no GPU state is needed).  The per-iteration cost at each
     sampled level (two-iteration minus one-iteration wall time) is fitted as
     a + b*FMAs and multiplied out over the per-level iteration counts of the
-    schedule (level_counts, the same on both sides by the parity tests)."""
+    schedule (level_counts, from the oracle's own complete run)."""
     import numpy as np
     import oracle
     side, D = wl["side"], wl["D"]
     N = side * side
     phis = oracle.levels(side, side)
     first_it = np.concatenate([[0], np.cumsum(level_counts)[:-1]])
-    targets = [phis[0], 100.0, 10.0, 1.0]
+    targets = list(radii) if radii else [phis[0], 100.0, 10.0, 1.0]
     sample_levels = sorted({int(np.argmin(np.abs(phis - t))) for t in targets})
     # the oracle's initial placement: Gaussian i at position pi0(i)
     perm0 = np.empty(N, np.int32)
@@ -402,15 +441,8 @@ def run_plas(args):
         "clocks": ck,
     }
     if args.cpu_baseline and world == 1:
-        counts = None
         try:
-            tr = plas.sort(x, side, side, carried=None, seed=seed, trace_cap=1 << 18)
-            counts = np.bincount(tr.trace_level.cpu().numpy(), minlength=st0["levels"])
-            import oracle
-            proj_ms, sample, cpu_s = oracle_projection(x_np, wl, seed, counts)
-            line["cpu_baseline"] = {"value": round(proj_ms, 1), "unit": "ms", "cores": oracle.num_threads(),
-                                    "kind": "oracle", "sample": sample, "cpu_seconds": round(cpu_s, 1),
-                                    "projected": True}
+            line["cpu_baseline"] = cpu_baseline(x_np, args.workload, wl)
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"value": None, "error": repr(e)}
     print(json.dumps(line), flush=True)
@@ -426,18 +458,18 @@ def run_reference(args):
         if pg is not None:
             pg.destroy_process_group()
         return
-    import torch
     import oracle
-    import paper_2312_13299_gb300 as plas
     oracle.build()
     wl = WORKLOADS[args.workload]
-    side = wl["side"]
     x_np, _ = make_inputs(wl, seed=0)
-    torch.cuda.set_device(local)
-    plas.load()
-    x = torch.from_numpy(x_np).cuda()
-    tr = plas.sort(x, side, side, seed=0, trace_cap=1 << 18)
-    counts = np.bincount(tr.trace_level.cpu().numpy(), minlength=len(oracle.levels(side, side)))
+    counts, src = oracle_level_counts(args.workload)
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no oracle fixture {os.path.relpath(src, ROOT)} for this workload"}), flush=True)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    oracle.set_num_threads(len(os.sched_getaffinity(0)))
     vals = []
     sample = ""
     for i in range(args.warmup + args.steps):
@@ -451,7 +483,8 @@ def run_reference(args):
             "data": "synthetic (seeded numpy; 3DGS-shaped attributes, no dataset)",
             "config": {"workload": wl["desc"]},
             "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "projected": True,
+                             "level_counts": f"oracle fixture {os.path.relpath(src, ROOT)}"},
             "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if pg is not None:

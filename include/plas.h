@@ -348,11 +348,24 @@ int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, in
  * 8192 x 8192); larger grids return PLAS_ERR_INVALID_ARG.  The call
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  Arguments, layout and errors as for
- * plas_smooth_loss_fwd.
+ * (cudaGetSymbolAddress) with that device current and caches it (threads
+ * that race on that first call store the same address); make that first
+ * call before any stream capture.  A cudaDeviceReset invalidates the cached
+ * address: do not use this entry point on a device after resetting it.
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ *
+ * Result: bit-identical to plas_smooth_loss_fwd whenever the regular call's
+ * row bands of 32 rows fit the array, i.e. ceil(W / (8 G)) * ceil(H / 32) <=
+ * 65536 with G = floor(256 / C) (channel-last tiles of the ksize <= 15,
+ * C <= 256, 16-byte-aligned path), and always on the strip path (ksize > 15,
+ * C > 256 or a misaligned x).  Otherwise the bands are taller, the FP64
+ * partial sums are added in another grouping, and the value agrees within
+ * rounding (relative 1e-12 in practice; the tests allow 1e-5).  Arguments,
+ * layout and errors as for plas_smooth_loss_fwd; grids whose strip-path
+ * launch would need more than 65535 CTA rows (H > 2,097,120 with ksize > 15,
+ * C > 256 or a misaligned x) return PLAS_ERR_INVALID_ARG on every loss entry
+ * point.
  */
 int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigma, int ksize,
                                  const float* ch_weights, float* loss, void* stream);
@@ -386,11 +399,11 @@ int plas_grid_select(const float* opacity, long long N, int stride, int32_t* kee
                      void* workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
-/* quantisation of the sorted attribute grids (Sec. 3.3)                   */
+/* quantisation of the sorted attribute grids (Sec. 3.4)                   */
 /* ---------------------------------------------------------------------- */
 /*
  * After training, each attribute channel of the sorted grid is clipped to a
- * range and rounded to the nearest of q equally spaced values (Sec. 3.3,
+ * range and rounded to the nearest of q equally spaced values (Sec. 3.4,
  * "Quantization & Compression"; the paper's q: 2^14 for coordinates, 2^6
  * for scale, opacity and rotation, 2^5 for the SH rest; its clip ranges:
  * DC colour [-2, 4], opacity [-6, 12], SH rest [-1, 1], rotation [-1, 2]).

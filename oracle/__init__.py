@@ -128,6 +128,7 @@ def lib():
                                        P(ctypes.c_ushort)]
             L.orc_dequantize.argtypes = [P(ctypes.c_ushort), ctypes.c_long, i, f, f, P(i), f]
             L.orc_num_threads.restype = i
+            L.orc_set_num_threads.argtypes = [i]
             _lib = L
     return _lib
 
@@ -357,7 +358,7 @@ def grid_select(opacity_logit: np.ndarray):
 
 
 def quantize(x: np.ndarray, lo, hi, q) -> np.ndarray:
-    """Sec. 3.3 quantisation codes (uint16) of an [N, C] float32 array."""
+    """Sec. 3.4 quantisation codes (uint16) of an [N, C] float32 array."""
     x = _f32(x)
     C = x.shape[-1]
     n = x.size // C
@@ -371,7 +372,7 @@ def quantize(x: np.ndarray, lo, hi, q) -> np.ndarray:
 
 
 def dequantize(codes: np.ndarray, lo, hi, q) -> np.ndarray:
-    """Sec. 3.3: the float32 value of each code of an [N, C] uint16 array."""
+    """Sec. 3.4: the float32 value of each code of an [N, C] uint16 array."""
     codes = np.ascontiguousarray(codes, np.uint16)
     C = codes.shape[-1]
     n = codes.size // C
@@ -385,3 +386,8 @@ def dequantize(codes: np.ndarray, lo, hi, q) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))

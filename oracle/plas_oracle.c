@@ -815,7 +815,7 @@ double orc_smooth_loss64_huber(const double* x, int H, int W, int C, double sigm
     return L;
 }
 
-/* Quantisation of Sec. 3.3: clip channel c to [lo_c, hi_c], map linearly to
+/* Quantisation of Sec. 3.4: clip channel c to [lo_c, hi_c], map linearly to
  * [0, 1] and round to the nearest of q_c equally spaced values (FP32, the
  * integer decided by rounding half to even; hi == lo gives 0).  Written
  * out as the definition; fmaxf/fminf send NaN to the bound. */
@@ -834,7 +834,7 @@ void orc_quantize(const float* x, long n, int C, const float* lo, const float* h
     }
 }
 
-/* The value a code stands for (the inverse step of Sec. 3.3): level k of
+/* The value a code stands for (the inverse step of Sec. 3.4): level k of
  * channel c is lo_c + k * ((hi_c - lo_c) / (q_c - 1)) in FP32 (lo_c when the
  * range is degenerate). */
 void orc_dequantize(const unsigned short* codes, long n, int C, const float* lo, const float* hi,
@@ -915,5 +915,17 @@ int orc_num_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Threads the parallel loops use from now on (test and timing plumbing: the
+ * results do not depend on it, every parallel loop writes independent
+ * outputs or sums integers). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }

@@ -545,7 +545,7 @@ def _quant_args(C, lo, hi, q):
 
 
 def quantize(x: torch.Tensor, lo, hi, q) -> torch.Tensor:
-    """Sec. 3.3 quantisation of an [N, C] (or [..., C]) float32 grid: clip
+    """Sec. 3.4 quantisation of an [N, C] (or [..., C]) float32 grid: clip
     channel c to [lo[c], hi[c]] and round to the nearest of q[c] levels.
     Returns the codes as int16 storage holding uint16 values (view with
     .to(torch.int32) & 0xFFFF to read them)."""

@@ -27,6 +27,7 @@
 // partial sums are FP32 over at most (2h+1) x 8 terms, then FP64 per CTA,
 // reduced in a fixed order.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -427,6 +428,7 @@ static bool set_smem_attr(size_t bytes) {
 // 16-byte aligned input (row bands chosen so that the grid has at most
 // max_partials CTAs), else the shared-memory strip kernel.
 struct Plan {
+    bool ok = true;  // false: the grid needs more than 65535 CTA rows
     bool staged = false;
     dim3 grid;
     int band = 0;
@@ -436,6 +438,7 @@ struct Plan {
 };
 
 constexpr size_t kSgMaxSmem = 160 * 1024;
+constexpr long long kMaxGridY = 65535;  // CUDA's limit on gridDim.y
 
 static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_partials) {
     Plan p;
@@ -445,9 +448,12 @@ static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_p
         const int slot_f = ((span + 6) / 4) * 4;
         const size_t smem = (size_t)sg_slots(h) * slot_f * sizeof(float);
         const long long gx = (W + kSgCells * G - 1) / (kSgCells * G);
+        // row bands of 32 rows, taller where the CTA count (one partial each)
+        // would exceed max_partials or the grid's y extent CUDA's 65535
         int band = 32;
-        while (gx * ((H + band - 1) / band) > max_partials && band < H) band *= 2;
-        if (smem <= kSgMaxSmem && gx * ((H + band - 1) / band) <= max_partials) {
+        auto rows = [&](int b) { return (long long)((H + (long long)b - 1) / b); };
+        while ((gx * rows(band) > max_partials || rows(band) > kMaxGridY) && band < H) band *= 2;
+        if (smem <= kSgMaxSmem && gx * rows(band) <= max_partials && rows(band) <= kMaxGridY) {
             p.staged = true;
             p.G = G;
             p.slot_f = slot_f;
@@ -459,9 +465,15 @@ static Plan plan_for(const float* u, int H, int W, int C, int h, long long max_p
         }
     }
     p.grid = grid_of(H, W);
+    p.ok = (H + kTYS - 1) / kTYS <= kMaxGridY;
     p.smem = smem_bytes(C, h);
     p.partials = (long long)p.grid.x * p.grid.y;
     return p;
+}
+
+static int plan_error() {
+    plas::set_last_error("grid too tall: the strip kernel needs ceil(H/32) <= 65535");
+    return PLAS_ERR_INVALID_ARG;
 }
 
 template <int HH, bool GRAD, bool HUBER, bool WRITE>
@@ -535,25 +547,31 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
 
 // Device address of g_noalloc_partials for the current device.  In host code
 // the symbol is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// cache is atomic: threads that race on a device's first call each look the
+// address up and store the same value.  A cudaDeviceReset of a device makes
+// its cached address stale; the allocation-free entry point is not meant to
+// be used across one.
 static double* noalloc_partials(int* err) {
-    static double* addr[64] = {nullptr};
+    static std::atomic<double*> addr[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         *err = PLAS_ERR_CUDA;
         return nullptr;
     }
-    if (!addr[dev]) {
+    double* a = addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess) {
             cudaGetLastError();
             *err = PLAS_ERR_CUDA;
             return nullptr;
         }
-        addr[dev] = (double*)p;
+        a = (double*)p;
+        addr[dev].store(a, std::memory_order_release);
     }
     *err = PLAS_OK;
-    return addr[dev];
+    return a;
 }
 
 }  // namespace plas_loss
@@ -579,6 +597,7 @@ int plas_smooth_loss_fwd_ex(const float* x, int H, int W, int C, float sigma, in
     cudaStream_t st = (cudaStream_t)stream;
     const int h = ksize / 2;
     const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
+    if (!p.ok) return plan_error();
     const size_t need = (size_t)p.partials * sizeof(double);
     void* mem = workspace;
     if (mem) {
@@ -619,6 +638,9 @@ int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, in
     }
     if (!grad_loss || !grad_x) { plas::set_last_error("grad_loss / grad_x is NULL"); return PLAS_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
+    const int h = ksize / 2;
+    const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
+    if (!p.ok) return plan_error();
     const size_t need = ws_bytes_for(H, W, C);
     void* mem = workspace;
     if (mem) {
@@ -632,8 +654,6 @@ int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, in
         return PLAS_ERR_OOM;
     }
     float* r = (float*)((char*)mem + partial_bytes(H, W, C));
-    const int h = ksize / 2;
-    const Plan p = plan_for(x, H, W, C, h, 1LL << 40);
     const double inv_m = 1.0 / ((double)H * W * C);
     const Taps tp = make_taps(sigma, ksize);
     // pass 1: r = x - B x (clamped to [-delta, delta] for Huber); the
@@ -691,6 +711,7 @@ int plas_smooth_loss_fwd_noalloc(const float* x, int H, int W, int C, float sigm
     const int h = ksize / 2;
     // taller row bands keep the CTA count (one partial each) within the array
     const Plan p = plan_for(x, H, W, C, h, kNoAllocMaxPartials);
+    if (!p.ok) return plan_error();
     cudaStream_t st = (cudaStream_t)stream;
     const double inv_m = 1.0 / ((double)H * W * C);
     // every CTA writes its own partial, so the array needs no clearing

@@ -1,4 +1,4 @@
-// quant_kernels.cu -- the quantisation step after the sort (Sec. 3.3
+// quant_kernels.cu -- the quantisation step after the sort (Sec. 3.4
 // "Quantization & Compression" of Morgenstern et al., arXiv 2312.13299):
 // every attribute channel of the sorted grid is clipped to a range and
 // rounded to the nearest of q equally spaced values, giving the integer

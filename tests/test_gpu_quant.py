@@ -1,4 +1,4 @@
-"""Quantisation of the sorted attribute grids (Sec. 3.3) on the GPU: codes
+"""Quantisation of the sorted attribute grids (Sec. 3.4) on the GPU: codes
 bit-exact against the oracle (the integer is decided in FP32 on both sides),
 the round trip within half a level, and argument checks."""
 import numpy as np

@@ -67,3 +67,18 @@ def test_permutation_check_argument_errors(lib):
     assert lib.plas_check_permutation(None, -1, None, None) == _lib.PLAS_ERR_INVALID_ARG
     assert lib.plas_check_permutation(None, 5, None, None) == _lib.PLAS_ERR_INVALID_ARG
     assert lib.plas_check_permutation(None, (1 << 30) + 1, None, None) == _lib.PLAS_ERR_INVALID_ARG
+
+
+def test_loss_rejects_grids_taller_than_the_launch_limit(lib):
+    """The strip kernel of the smoothness loss (ksize > 15) runs one CTA row
+    per 32 grid rows; a grid that would need more than CUDA's 65535 CTA rows
+    is rejected before any launch or allocation (the pointers are never
+    dereferenced)."""
+    fake = ctypes.c_void_p(256)
+    H = 65536 * 32  # ceil(H / 32) = 65536 > 65535
+    for fn in ("plas_smooth_loss_fwd",):
+        rc = getattr(lib, fn)(fake, H, 1, 1, 1.0, 17, None, fake, None, 0, None)
+        assert rc == _lib.PLAS_ERR_INVALID_ARG
+        assert b"65535" in lib.plas_last_error()
+    rc = lib.plas_smooth_loss_bwd(fake, H, 1, 1, 1.0, 17, None, fake, fake, None, 0, None)
+    assert rc == _lib.PLAS_ERR_INVALID_ARG

@@ -1,4 +1,4 @@
-"""Pins of the oracle's quantisation (Sec. 3.3: clip each attribute channel
+"""Pins of the oracle's quantisation (Sec. 3.4: clip each attribute channel
 to a range, round to the nearest of q equally spaced values).
 
 * Values on the levels map to their own index (exactly representable grid).
