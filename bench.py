@@ -338,9 +338,9 @@ def run_plas(args):
     if args.tune == "auto":
         tune = plas.autotune(side, side, D)
     else:
-        sb, mb, per = (int(v) for v in args.tune.split(","))
+        sb, mb, per, *tma = (int(v) for v in args.tune.split(","))
         plas.set_tuning(side, side, D, fir_small_below=sb, fir_medium_below=mb,
-                        assign_ctas_per_sm=per)
+                        assign_ctas_per_sm=per, large_tma=tma[0] if tma else None)
         tune = plas.get_tuning(side, side, D)
     t_tune = time.perf_counter() - t_tune
 
@@ -378,7 +378,11 @@ def run_plas(args):
     launches = int(sum(st["launches"] for st in stats_plain))
     # per-kernel durations for the roofline: the same K sorts again with a
     # CUDA event pair around every launch (their own timed region)
+    n_prof = args.steps
+    args_steps = args.steps
+    args.steps = min(args.steps, 3)
     prof_ms, stats, ck_prof = timed(True)
+    n_prof, args.steps = args.steps, args_steps
 
     # end to end: pinned host inputs in, permutation + carried out, per step
     xh = torch.from_numpy(x_np).pin_memory()
@@ -413,8 +417,8 @@ def run_plas(args):
         return
     peaks, psrc = _peaks()
     rl, per_kernel = roofline(stats, peaks, psrc, ck_prof or ck, args.workload)
-    rl["timing"] = (f"CUDA events around every launch over {args.steps} further sorts "
-                    f"({prof_ms / args.steps:.1f} ms per sort with the events)")
+    rl["timing"] = (f"CUDA events around every launch over {n_prof} further sorts "
+                    f"({prof_ms / n_prof:.1f} ms per sort with the events)")
     st0 = stats_plain[-1]
     line = {
         "metric": METRIC, "value": round(ms_per_sort, 3), "unit": "ms", "n_gpus": world,
@@ -445,6 +449,12 @@ def run_plas(args):
             line["cpu_baseline"] = cpu_baseline(x_np, args.workload, wl)
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"value": None, "error": repr(e)}
+    if args.serve_in_bench and world == 1:
+        try:
+            line["serve"] = serve_compare(args.requests, ["poisson", "burst"],
+                                          [p for p in args.serve_policy.split(",") if p], args.sweeps)
+        except Exception as e:  # reported, never silently replaced
+            line["serve"] = {"error": repr(e)}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
@@ -491,23 +501,22 @@ def run_reference(args):
         pg.destroy_process_group()
 
 
-def run_serve(args):
-    """Served stream: n requests (sides U{128..1024}, 14 sort + 45 carried
-    channels) under a 40 GB admission budget, through the server (continuous
-    batching, one run per scheduling policy) and through the plain path (one
-    plas_sort per request, first come first served).  Two arrival patterns:
-    Poisson arrivals at 0.8 x the plain path's capacity (mean service time of
-    the side distribution, from a power-law fit of measured plain sorts), and a
-    burst (every request at t = 0) for throughput.  Latency = completion time -
-    arrival time (host clock)."""
+def serve_compare(n, patterns, policies, sweeps, budget_bytes=40 * 10 ** 9):
+    """Served stream against the plain path on one GPU: n requests (sides
+    U{128..1024}, 14 sort + 45 carried channels, seeded) under an admission
+    budget, through the server (continuous batching, one run per policy) and
+    through the plain path (one plas_sort per request, first come first
+    served).  Arrival patterns: 'poisson' at 0.8 x the plain path's capacity
+    (mean service time of the side distribution, from a power-law fit of
+    measured plain sorts), 'overload' Poisson at 1.25 x that capacity, and
+    'burst' (every request at t = 0).  Latency = completion - arrival (host
+    clock).  Every served result (permutation and carried attributes) is
+    compared with the plain path's result of the same request."""
     import numpy as np
     import torch
     import paper_2312_13299_gb300 as plas
     from paper_2312_13299_gb300 import synth
-    plas.load()
-    dev = torch.device("cuda", 0)
-    n = args.requests
-    # plain service time vs side: t = a * side^b
+    dev = torch.device("cuda", torch.cuda.current_device())
     fit_sides = [128, 384, 768]
     ts = []
     for side in fit_sides:
@@ -528,6 +537,7 @@ def run_serve(args):
         x, c = synth.gaussians_3dgs(side * side, seed=1000 + i)
         inputs.append((side, torch.from_numpy(x).to(dev), torch.from_numpy(c).to(dev), i))
     torch.cuda.synchronize()
+    ref = {}
 
     def plain(arrivals):
         lat, t0, cells_iters = [], time.perf_counter(), 0
@@ -538,55 +548,71 @@ def run_serve(args):
             torch.cuda.synchronize()
             lat.append(time.perf_counter() - t0 - arr)
             cells_iters += side * side * r.state["it"]
-        return lat, time.perf_counter() - t0, cells_iters
+            ref[i] = (r.perm, r.carried)
+        return lat, time.perf_counter() - t0, cells_iters, None
 
     def served(arrivals, policy):
-        srv = plas.Server(14, mem_budget=40 * 10 ** 9, policy=policy)
-        lat, t0, nxt, pending, cells_iters = {}, time.perf_counter(), 0, {}, 0
+        srv = plas.Server(14, mem_budget=budget_bytes, policy=policy)
+        lat, t0, nxt, pending, cells_iters, same = {}, time.perf_counter(), 0, {}, 0, 0
         while len(lat) < n:
             now = time.perf_counter() - t0
             while nxt < n and arrivals[nxt] <= now:
                 side, x, c, i = inputs[nxt]
-                pending[srv.submit(x, side, side, c, seed=i)] = (arrivals[nxt], side)
+                pending[srv.submit(x, side, side, c, seed=i)] = (arrivals[nxt], side, i)
                 nxt += 1
             if not pending:
                 time.sleep(0.0005)
                 continue
-            for tk, res in srv.step(sweeps=args.sweeps):
-                arr, side = pending.pop(tk)
+            for tk, res in srv.step(sweeps=sweeps):
+                arr, side, i = pending.pop(tk)
                 lat[tk] = time.perf_counter() - t0 - arr
                 cells_iters += side * side * res.state["it"]
+                if i in ref:
+                    same += int(torch.equal(res.perm, ref[i][0]) and torch.equal(res.carried, ref[i][1]))
+        wall = time.perf_counter() - t0
         srv.close()
-        return list(lat.values()), time.perf_counter() - t0, cells_iters
+        return list(lat.values()), wall, cells_iters, same
 
-    def summary(lat, wall, ci):
+    def summary(lat, wall, ci, same):
         lat = np.array(lat) * 1e3
-        return {"p50_ms": round(float(np.percentile(lat, 50)), 1),
-                "p99_ms": round(float(np.percentile(lat, 99)), 1),
-                "mean_ms": round(float(lat.mean()), 1), "wall_s": round(wall, 2),
-                "requests_per_s": round(n / wall, 3), "melem_iter_per_s": round(ci / wall / 1e6, 1)}
+        out = {"p50_ms": round(float(np.percentile(lat, 50)), 1),
+               "p99_ms": round(float(np.percentile(lat, 99)), 1),
+               "mean_ms": round(float(lat.mean()), 1), "wall_s": round(wall, 2),
+               "requests_per_s": round(n / wall, 3), "melem_iter_per_s": round(ci / wall / 1e6, 1)}
+        if same is not None:
+            out["results_equal_plain"] = f"{same}/{n}"
+        return out
 
-    patterns = {"poisson": [a for a, _ in base], "burst": [0.0] * n}
-    policies = [p for p in args.policies.split(",") if p]
+    pats = {"poisson": [a for a, _ in base], "overload": [a * 0.8 / 1.25 for a, _ in base],
+            "burst": [0.0] * n}
     out = {}
-    for pat in [p for p in args.patterns.split(",") if p]:
-        arr = patterns[pat]
+    for pat in patterns:
+        arr = pats[pat]
         out[pat] = {"plain": summary(*plain(arr))}
         for pol in policies:
             out[pat]["served_" + pol] = summary(*served(arr, pol))
+    return {"workload": f"{n} requests, sides U{{128..1024}}, 14 sort + 45 carried fp32, "
+                        f"{budget_bytes / 1e9:.0f} GB admission budget, seed 0",
+            "poisson_rate_per_s": round(rate, 3),
+            "plain_service_fit": f"t = {math.exp(loga):.3g} * side^{b:.2f} s "
+                                 f"(mean {mean_service * 1e3:.0f} ms over the side distribution)",
+            "sweeps_per_step": sweeps, "results": out}
+
+
+def run_serve(args):
+    """The served stream on its own JSON line (every policy and pattern)."""
+    import paper_2312_13299_gb300 as plas
+    plas.load()
+    policies = [p for p in args.policies.split(",") if p]
+    patterns = [p for p in args.patterns.split(",") if p]
+    res = serve_compare(args.requests, patterns, policies, args.sweeps)
     first = policies[0] if policies else None
-    head = out.get("poisson", out.get("burst", {}))
+    head = res["results"].get("poisson", next(iter(res["results"].values()), {}))
     line = {"metric": "served p50/p99 latency of PLAS sort requests",
             "value": head.get("served_" + first, {}).get("p99_ms") if first else None,
             "unit": f"ms (p99, served, {first})", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic (seeded numpy; 3DGS-shaped attributes)",
-            "config": {"workload": f"{n} requests, sides U{{128..1024}}, 14 sort + 45 carried fp32, "
-                                   "40 GB admission budget",
-                       "poisson_rate_per_s": round(rate, 3),
-                       "plain_service_fit": f"t = {math.exp(loga):.3g} * side^{b:.2f} s "
-                                            f"(mean {mean_service * 1e3:.0f} ms over the side distribution)",
-                       "sweeps_per_step": args.sweeps},
-            "results": out}
+            "config": {k: v for k, v in res.items() if k != "results"}, "results": res["results"]}
     print(json.dumps(line), flush=True)
 
 
@@ -748,9 +774,9 @@ def run_ncu_case(args):
     x_np, _ = make_inputs(wl, seed=0)
     x = torch.from_numpy(x_np).cuda()
     if args.tune != "auto":  # pinned launch shapes (the default shapes otherwise)
-        sb, mb, per = (int(v) for v in args.tune.split(","))
+        sb, mb, per, *tma = (int(v) for v in args.tune.split(","))
         plas.set_tuning(side, side, wl["D"], fir_small_below=sb, fir_medium_below=mb,
-                        assign_ctas_per_sm=per)
+                        assign_ctas_per_sm=per, large_tma=tma[0] if tma else None)
     r = plas.sort(x, side, side, seed=0,
                   schedule=plas.Schedule(max_iters=args.ncu_case, phi0=args.phi0,
                                          target_mode=1 if args.target == "box" else 0),
@@ -773,7 +799,7 @@ def main():
     ap.add_argument("--target", default="gaussian", choices=["gaussian", "box"],
                     help="low-pass target of the sort: the Gaussian (default) or the box variant")
     ap.add_argument("--tune", default="auto", help="'auto' (run the autotuner) or "
-                    "SMALL_BELOW,MEDIUM_BELOW,CTAS_PER_SM to pin the launch shapes")
+                    "SMALL_BELOW,MEDIUM_BELOW,CTAS_PER_SM[,LARGE_TMA] to pin the launch shapes")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="run one sort of the workload capped at ITERS iterations and exit "
                          "(a small, bounded program for ncu captures; prints nothing)")
@@ -796,7 +822,12 @@ def main():
     ap.add_argument("--sweeps", type=int, default=8, help="sweeps per server step")
     ap.add_argument("--policies", default="fifo_fill,shortest_first,all",
                     help="with --serve: server policies to run")
-    ap.add_argument("--patterns", default="poisson,burst", help="with --serve: arrival patterns")
+    ap.add_argument("--patterns", default="poisson,burst", help="with --serve: arrival patterns "
+                    "(poisson = 0.8 x plain capacity, overload = 1.25 x, burst)")
+    ap.add_argument("--no-serve", dest="serve_in_bench", action="store_false",
+                    help="leave the served-stream comparison out of the default line")
+    ap.add_argument("--serve-policy", default="all",
+                    help="server policies of the default line's served-stream comparison")
     args = ap.parse_args()
     if args.ncu_case > 0:
         run_ncu_case(args)

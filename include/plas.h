@@ -39,7 +39,8 @@ extern "C" {
 #define PLAS_ERR_INVALID_ARG (-1) /* bad size, NULL pointer, misalignment   */
 #define PLAS_ERR_OOM (-2)         /* device allocation failed               */
 #define PLAS_ERR_CUDA (-3)        /* a CUDA runtime call failed             */
-#define PLAS_ERR_TIMEOUT (-4)     /* a bounded device wait gave up          */
+#define PLAS_ERR_TIMEOUT (-4)     /* a bounded device wait gave up (the     */
+                                  /* target kernel's pipeline waits, ~2 s)  */
 #define PLAS_ERR_NONFINITE (-5)   /* input holds NaN or +-Inf               */
 #define PLAS_ERR_BUDGET (-6)      /* batch does not fit its memory budget   */
 #define PLAS_ERR_INTERNAL (-7)    /* an internal consistency check failed   */
@@ -201,7 +202,10 @@ size_t plas_sort_workspace_bytes_ex(int H, int W, int D, const plas_schedule* sc
  * sched->iters_per_poll iterations, so it returns once the whole sort has
  * run on the device.  Errors: PLAS_ERR_INVALID_ARG (sizes, NULL, D range,
  * misaligned pointers), PLAS_ERR_NONFINITE (x holds NaN/Inf; nothing is
- * written to the outputs), PLAS_ERR_OOM, PLAS_ERR_CUDA.
+ * written to the outputs), PLAS_ERR_OOM, PLAS_ERR_CUDA, PLAS_ERR_TIMEOUT (a
+ * wait inside the large-radius target kernel saw no progress for about two
+ * seconds; the kernel gave up and left the GPU usable), PLAS_ERR_INTERNAL
+ * (the host saw a grid make no progress over five state read-backs).
  */
 int plas_sort(const float* x, int H, int W, int D, const float* weights,
               const float* carried, int C, uint64_t seed, const plas_schedule* sched,
@@ -259,8 +263,8 @@ int plas_target_box(const float* x, int H, int W, int D, const float* weights, i
                     const int32_t* perm, double phi, float* T, void* stream);
 
 /*
- * plas_group_permutation -- the grouping permutation of Sec. 3.1 ("a random
- * permutation of all elements from a block", shared by all blocks): out[m]
+ * plas_group_permutation -- the grouping permutation of Sec. 3.1 (one random
+ * ordering of the cells of a block, the same for every block): out[m]
  * for m < n, a keyed bijection of [0, n) (six-round Feistel network driven
  * by Philox4x32-10, cycle walking).  tag/counter select the stream (3 and
  * the iteration for groupings, 1 and 0 for the initial placement).
@@ -479,7 +483,8 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   shape on the current device would use (the defaults 8, 96 and 8 when
  *   nothing is installed).  A radius r takes the direct kernel when
  *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
- *   the 128-row one.  Thread-safe.
+ *   the 128-row one, which streams with tensor copies when large_tma is 1
+ *   and the grid allows it.  Thread-safe.
  */
 #define PLAS_TUNE_MAX_RADII 16
 #define PLAS_TUNE_ASSIGN_CANDIDATES 4
@@ -495,6 +500,13 @@ typedef struct plas_tuning {
     float fir_large_us[PLAS_TUNE_MAX_RADII];  /* both passes, 128-row tiling  */
     int assign_per_sm[PLAS_TUNE_ASSIGN_CANDIDATES];
     float assign_us[PLAS_TUNE_ASSIGN_CANDIDATES]; /* sum over the two radii   */
+    int large_tma;          /* 1: the large tiling streams its input rows with */
+                            /* tensor copies (persistent CTAs, single grids of */
+                            /* an even D with an instantiated row box); 0: the */
+                            /* chunked ring.  Default 1                        */
+    float fir_large_ring_us[PLAS_TUNE_MAX_RADII]; /* both passes, chunked    */
+    float fir_large_tma_us[PLAS_TUNE_MAX_RADII];  /* both passes, tensor      */
+                                                  /* copies; -1: not eligible */
 } plas_tuning;
 int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out);
 int plas_set_tuning(int H, int W, int D, const plas_tuning* t /* host or NULL */);
@@ -535,6 +547,15 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out);
  *     large radius fills a sweep; grids at small radii share one);
  *   PLAS_SERVE_SHORTEST_FIRST: least estimated work left first, same fill;
  *   PLAS_SERVE_ALL: every admitted grid in every sweep.
+ *   PLAS_SERVE_CONCURRENT: up to 16 admitted requests each advance on a
+ *     stream of their own, in graph-replayed batches of 'sweeps' iterations
+ *     with two batches in flight, so every request moves at its own pace.
+ *     The oldest admitted request's stream has the highest priority and the
+ *     others the lowest: its CTAs get the SMs first, as on the plain path,
+ *     and younger requests fill the SMs it leaves idle.  When it finishes,
+ *     the next oldest is moved to a high-priority stream.  A step feeds
+ *     every lane and waits only when no lane can move.  Switching to or from
+ *     this policy needs a server with nothing admitted.
  *   PLAS_ERR_INVALID_ARG for an unknown policy.
  * plas_server_cancel: withdraws a request that is queued or running.  A
  *   queued request is removed at once; a running one leaves the sweeps at
@@ -553,7 +574,8 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out);
  *   still queued or running are abandoned (their outputs are undefined).
  */
 typedef struct plas_server plas_server;
-enum { PLAS_SERVE_FIFO_FILL = 0, PLAS_SERVE_SHORTEST_FIRST = 1, PLAS_SERVE_ALL = 2 };
+enum { PLAS_SERVE_FIFO_FILL = 0, PLAS_SERVE_SHORTEST_FIRST = 1, PLAS_SERVE_ALL = 2,
+       PLAS_SERVE_CONCURRENT = 3 };
 int plas_server_create(int D, const float* weights, const plas_schedule* sched,
                        size_t mem_budget, void* stream, plas_server** out);
 int plas_server_set_policy(plas_server* srv, int policy);
@@ -568,6 +590,21 @@ int plas_server_destroy(plas_server* srv);
 /* ---------------------------------------------------------------------- */
 const char* plas_status_string(int status);
 const char* plas_last_error(void);  /* thread-local; "" if none */
+/*
+ * plas_debug_inject -- host-side fault injection for tests of the error
+ * paths; it never faults or stalls the GPU.  The paper has no counterpart.
+ *   kind 0: clear every injection (count ignored);
+ *   kind 1: the count-th device allocation made by the library from now on
+ *           (workspaces, descriptor arrays, scratch) fails as if the device
+ *           were out of memory: the call returns PLAS_ERR_OOM after freeing
+ *           what it had allocated;
+ *   kind 2: the sweep engine's next count state read-backs are frozen (the
+ *           host keeps its previous copy), so its progress check sees grids
+ *           that do not advance and the call returns PLAS_ERR_INTERNAL.
+ * Process-wide (all threads).  Returns PLAS_OK or PLAS_ERR_INVALID_ARG
+ * (unknown kind, count < 1).
+ */
+int plas_debug_inject(int kind, long long count);
 int plas_version(void);              /* major*10000 + minor*100 + patch */
 
 #ifdef __cplusplus

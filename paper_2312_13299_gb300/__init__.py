@@ -270,7 +270,10 @@ def _tuning_dict(t: "_lib.plas_tuning") -> dict:
             "fir_medium_us": [round(v, 2) for v in t.fir_medium_us[:n]],
             "fir_large_us": [round(v, 2) for v in t.fir_large_us[:n]],
             "assign_per_sm": list(t.assign_per_sm) if n else [],
-            "assign_us": [round(v, 2) for v in t.assign_us] if n else []}
+            "assign_us": [round(v, 2) for v in t.assign_us] if n else [],
+            "large_tma": int(t.large_tma),
+            "fir_large_ring_us": [round(v, 2) for v in t.fir_large_ring_us[:n]],
+            "fir_large_tma_us": [round(v, 2) for v in t.fir_large_tma_us[:n]]}
 
 
 def autotune(H: int, W: int, D: int, device=None) -> dict:
@@ -287,12 +290,14 @@ def autotune(H: int, W: int, D: int, device=None) -> dict:
 
 def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
                assign_ctas_per_sm: Optional[int] = None,
-               fir_medium_below: Optional[int] = None) -> None:
+               fir_medium_below: Optional[int] = None, large_tma: Optional[bool] = None) -> None:
     """Install launch shapes for (H, W, D) on the current device; with every
     argument None the entry is removed (defaults apply again).  A radius r
     takes the direct FIR kernel when r < fir_small_below, else the 64-row one
-    when r < fir_medium_below, else the 128-row one."""
-    if fir_small_below is None and assign_ctas_per_sm is None and fir_medium_below is None:
+    when r < fir_medium_below, else the 128-row one (with tensor copies when
+    large_tma is set and the grid allows it)."""
+    if (fir_small_below is None and assign_ctas_per_sm is None and fir_medium_below is None
+            and large_tma is None):
         check(load().plas_set_tuning(H, W, D, None), "plas_set_tuning")
         return
     cur = get_tuning(H, W, D)
@@ -301,6 +306,7 @@ def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
     t.fir_medium_below = cur["fir_medium_below"] if fir_medium_below is None else fir_medium_below
     t.assign_ctas_per_sm = (cur["assign_ctas_per_sm"] if assign_ctas_per_sm is None
                             else assign_ctas_per_sm)
+    t.large_tma = cur["large_tma"] if large_tma is None else int(bool(large_tma))
     check(load().plas_set_tuning(H, W, D, ctypes.byref(t)), "plas_set_tuning")
 
 
@@ -314,11 +320,12 @@ class Server:
     """Continuous batching of sort requests (plas_server_*): requests queue up,
     are admitted while their workspaces fit the device-memory budget, and
     advance together one iteration per sweep; 'policy' picks which admitted
-    grids each step advances (fifo_fill, shortest_first, all).  Results equal
+    grids each step advances (fifo_fill, shortest_first, all), or runs every
+    admitted request on a prioritised stream of its own (concurrent).  Results equal
     sort() of each request alone under every policy.  All work runs on the
     stream current at construction."""
 
-    POLICIES = {"fifo_fill": 0, "shortest_first": 1, "all": 2}
+    POLICIES = {"fifo_fill": 0, "shortest_first": 1, "all": 2, "concurrent": 3}
 
     def __init__(self, D: int, weights=None, schedule: Optional[Schedule] = None,
                  mem_budget: int = 0, device=None, policy: str = "fifo_fill"):
@@ -340,6 +347,14 @@ class Server:
         self._steps = 0
         if policy not in self.POLICIES:
             self.close()
+            raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
+        check(self._lib.plas_server_set_policy(self._h, self.POLICIES[policy]),
+              "plas_server_set_policy")
+
+    def _lib_policy(self, policy: str) -> None:
+        """Change the scheduling policy (the concurrent policy can only be
+        entered or left while nothing is admitted)."""
+        if policy not in self.POLICIES:
             raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
         check(self._lib.plas_server_set_policy(self._h, self.POLICIES[policy]),
               "plas_server_set_policy")

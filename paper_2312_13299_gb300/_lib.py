@@ -75,7 +75,9 @@ class plas_tuning(ctypes.Structure):
                 ("fir_medium_us", c_float * TUNE_MAX_RADII),
                 ("fir_large_us", c_float * TUNE_MAX_RADII),
                 ("assign_per_sm", c_int * TUNE_ASSIGN_CANDIDATES),
-                ("assign_us", c_float * TUNE_ASSIGN_CANDIDATES)]
+                ("assign_us", c_float * TUNE_ASSIGN_CANDIDATES), ("large_tma", c_int),
+                ("fir_large_ring_us", c_float * TUNE_MAX_RADII),
+                ("fir_large_tma_us", c_float * TUNE_MAX_RADII)]
 
 
 P = ctypes.POINTER
@@ -137,6 +139,7 @@ SIGNATURES = {
     "plas_status_string": (ctypes.c_char_p, [c_int]),
     "plas_last_error": (ctypes.c_char_p, []),
     "plas_version": (c_int, []),
+    "plas_debug_inject": (c_int, [c_int, c_ll]),
 }
 
 _lock = threading.Lock()

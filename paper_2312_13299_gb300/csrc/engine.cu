@@ -56,6 +56,7 @@ struct Slot {
     int nlev = 0;
     int ctas[kClsCount] = {0, 0, 0};
     Tuning tune;  // FIR tiling choice (one-grid sweeps)
+    FirTma tma;   // the large tiling's tensor maps (one-grid sweeps)
     bool active = false;
     bool cancel = false;  // served request cancelled while admitted
     DevState last{};
@@ -112,6 +113,26 @@ class Engine {
         for (auto& g : graph_)
             if (g.exec) cudaGraphExecDestroy(g.exec);
         if (cap_) cudaStreamDestroy(cap_);
+        if (!owned_host_.empty()) {
+            cudaStreamSynchronize(st_);  // no read-back may still target them
+            for (void* h : owned_host_) cudaFreeHost(h);
+        }
+    }
+
+    // Poll into pinned buffers of this engine instead of the calling
+    // thread's shared one (for engines that outlive a single call).
+    void own_host_buffers() { own_host_ = true; }
+
+    // Continue this engine's work on stream s, after everything already
+    // enqueued on its current stream (graphs launch into any stream).
+    int move_to_stream(cudaStream_t s) {
+        cudaEvent_t e = nullptr;
+        PLAS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        PLAS_CUDA(cudaEventRecord(e, st_));
+        PLAS_CUDA(cudaStreamWaitEvent(s, e, 0));
+        cudaEventDestroy(e);
+        st_ = s;
+        return PLAS_OK;
     }
 
     // Multi-grid descriptor arrays come from this arena when given (no
@@ -133,6 +154,7 @@ class Engine {
         sl->nlev = (int)sl->geo.lv.size();
         workspace_layout(H, W, D_, sl->nlev, sl->geo.table_floats, &sl->ws, sl->mem,
                          s_.target_mode == 1);
+        make_fir_tma(sl->ws.G, sl->ws.H1, H, W, D_, sl->geo.max_steps, &sl->tma);
         DevState init{};
         if (j.resume) {
             init.it = j.init.it;
@@ -245,13 +267,18 @@ class Engine {
         return PLAS_OK;
     }
 
+    // Whether poll 'buf' has landed (wait() then returns without blocking),
+    // and a wait for it that does not consume it.
+    bool poll_ready(int buf) const { return cudaEventQuery(ev_[buf]) != cudaErrorNotReady; }
+    void sync_poll(int buf) const { cudaEventSynchronize(ev_[buf]); }
+
     // Wait for poll 'buf' and store each polled grid's state.
     int wait(int buf) {
         PLAS_CUDA(cudaEventSynchronize(ev_[buf]));
         const size_t hb = kStateHeaderBytes;
         for (size_t i = 0; i < polled_[buf].size(); ++i) {
             Slot* sl = polled_[buf][i];
-            memcpy(&sl->last, polled_base_[buf] + i * hb, hb);
+            if (!injected_stall()) memcpy(&sl->last, polled_base_[buf] + i * hb, hb);
             if (!finished(*sl, s_)) {
                 sl->stuck = (sl->last.it == sl->last_it) ? sl->stuck + 1 : 0;
                 sl->last_it = sl->last.it;
@@ -350,6 +377,13 @@ class Engine {
         return e;
     }
 
+    // Tensor maps of the one grid a sweep advances (none for many grids).
+    const FirTma* tma_of(const SweepPlan& p) const {
+        return p.map[kClsFirY] == nullptr && active_.size() == 1 && active_[0]->tune.large_tma
+                   ? &active_[0]->tma
+                   : nullptr;
+    }
+
     // The launches of k sweeps (events only when profiling directly).
     void enqueue(const SweepPlan& p, cudaStream_t st, bool events) {
         for (int i = 0; i < p.k; ++i) {
@@ -360,10 +394,11 @@ class Engine {
                         if (s_.target_mode == 1)  // box target (single grid): all of it here
                             launch_box_target(p.grids, active_[0]->job.H, active_[0]->job.W, D_, nsm_, st);
                         else
-                            launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st);
+                            launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
                         break;
                     case kClsFirX:
-                        if (s_.target_mode != 1) launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st);
+                        if (s_.target_mode != 1)
+                            launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
                         break;
                     default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st); break;
                 }
@@ -416,8 +451,16 @@ class Engine {
 
     int host_buffers(size_t bytes) {
         void* h = nullptr;
-        cudaEvent_t unused[2];
-        if (int e = poll_buffers(bytes, &h, unused)) return e;
+        if (own_host_) {
+            // a buffer of this engine alone (engines that live side by side in
+            // one thread must not share the per-thread staging buffer); a
+            // grown buffer replaces the old one, which is freed with the engine
+            PLAS_CUDA(cudaMallocHost(&h, std::max<size_t>(bytes, 4096)));
+            owned_host_.push_back(h);
+        } else {
+            cudaEvent_t unused[2];
+            if (int e = poll_buffers(bytes, &h, unused)) return e;
+        }
         host_ = (char*)h;
         if (!ev_[0]) {
             PLAS_CUDA(cudaEventCreateWithFlags(&ev_[0], cudaEventDisableTiming));
@@ -460,7 +503,7 @@ class Engine {
             } else {
                 if (dmaps_ && dmaps_owned_) cudaFreeAsync(dmaps_, st_);  // stream-ordered
                 void* p = nullptr;
-                if (cudaMallocAsync(&p, need * 2, st_) != cudaSuccess) {
+                if (dev_alloc(&p, need * 2, st_) != cudaSuccess) {
                     cudaGetLastError();
                     return fail(PLAS_ERR_OOM, "descriptor allocation failed");
                 }
@@ -511,6 +554,8 @@ class Engine {
     cudaStream_t cap_ = nullptr;
     Graph graph_[kFirTilings];  // one per FIR tiling
     bool graphs_failed_ = false;
+    bool own_host_ = false;
+    std::vector<void*> owned_host_;
 
    public:
     long long captures_ = 0;
@@ -656,7 +701,7 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
         sl.mem = (char*)workspace;
     } else {
         void* mem = nullptr;
-        if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+        if (dev_alloc(&mem, need, st) != cudaSuccess) {
             cudaGetLastError();
             return fail(PLAS_ERR_OOM, "workspace allocation of %zu bytes failed", need);
         }
@@ -772,9 +817,22 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
         sl.mem = ws;
         if (int e = eng.admit(&sl)) return e;
         out->radius[i] = r;
-        for (int var : {kFirLargeRadius, kFirMediumRadius, kFirSmallRadius}) {
+        for (int var : {kFirLargeRadius + 100, kFirLargeRadius, kFirMediumRadius, kFirSmallRadius}) {
             if (var == kFirSmallRadius && r > kDirectTuneMaxR) {  // correct, but slow there
                 out->fir_small_us[i] = -1.0f;
+                continue;
+            }
+            if (var == kFirLargeRadius + 100) {  // the large tiling with tensor copies
+                out->fir_large_tma_us[i] = -1.0f;
+                if (!sl.tma.ok) continue;
+                const int c0 = fir_ctas(H, W * D, kFirLargeRadius), c1 = fir_ctas(W, H * D, kFirLargeRadius);
+                float us = 0.0f;
+                if (int e = time_us(st, a, b, kReps, [&] {
+                        launch_fir(0, sl.ws.ref, nullptr, c0, D, kFirLargeRadius, st, &sl.tma);
+                        launch_fir(1, sl.ws.ref, nullptr, c1, D, kFirLargeRadius, st, &sl.tma);
+                    }, &us))
+                    return e;
+                out->fir_large_tma_us[i] = us;
                 continue;
             }
             const int c0 = fir_ctas(H, W * D, var), c1 = fir_ctas(W, H * D, var);
@@ -800,6 +858,19 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
             }
         }
     }
+    // the large tiling: tensor copies where they are faster summed over the
+    // measured radii (both variants give the same bits)
+    double ring_sum = 0.0, tma_sum = 0.0;
+    bool tma_all = true;
+    for (size_t i = 0; i < radii.size(); ++i) {
+        out->fir_large_ring_us[i] = out->fir_large_us[i];
+        ring_sum += out->fir_large_us[i];
+        tma_sum += out->fir_large_tma_us[i];
+        tma_all = tma_all && out->fir_large_tma_us[i] > 0.0f;
+    }
+    const int large_tma = tma_all && tma_sum < ring_sum ? 1 : 0;
+    if (large_tma)
+        for (size_t i = 0; i < radii.size(); ++i) out->fir_large_us[i] = out->fir_large_tma_us[i];
     // the two thresholds (small <= medium) that minimise the summed time over
     // the measured radii
     Tuning best;
@@ -831,8 +902,10 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
     out->fir_small_below = best.small_below;
     out->fir_medium_below = best.medium_below;
     out->assign_ctas_per_sm = per_sm[best_c];
+    out->large_tma = large_tma;
     Tuning tu = best;
     tu.assign_per_sm = per_sm[best_c];
+    tu.large_tma = large_tma;
     install_tuning(H, W, D, &tu);
     return PLAS_OK;
 }
@@ -852,8 +925,8 @@ extern "C" int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out
     const size_t ws_bytes = sort_workspace_bytes(H, W, D, s);
     void* x = nullptr;
     void* ws = nullptr;
-    if (cudaMallocAsync(&x, (size_t)N * D * sizeof(float), st) != cudaSuccess ||
-        cudaMallocAsync(&ws, ws_bytes, st) != cudaSuccess) {
+    if (dev_alloc(&x, (size_t)N * D * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(&ws, ws_bytes, st) != cudaSuccess) {
         cudaGetLastError();
         if (x) cudaFreeAsync(x, st);
         return fail(PLAS_ERR_OOM, "autotune buffers");
@@ -937,7 +1010,7 @@ extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* 
         base = (char*)workspace;
     } else {
         void* p = nullptr;
-        if (cudaMallocAsync(&p, need, st) != cudaSuccess) {
+        if (dev_alloc(&p, need, st) != cudaSuccess) {
             cudaGetLastError();
             return fail(PLAS_ERR_OOM, "batch workspace allocation of %zu bytes failed", need);
         }
@@ -997,6 +1070,19 @@ struct plas_server {
     long long step_no = 0;
     int buf = 0;
     bool pending = false;  // a state read-back is in flight
+    // PLAS_SERVE_CONCURRENT: one lane (stream + engine) per admitted request
+    struct Lane {
+        std::unique_ptr<Slot> sl;
+        cudaStream_t st = nullptr;
+        std::unique_ptr<Engine> eng;
+        int buf = 0;
+        int inflight = 0;        // batches whose state read-back is not consumed
+        cudaEvent_t done = nullptr;  // after the outputs, once retired
+        bool head = false;       // on the high-priority stream
+        std::vector<cudaStream_t> old_streams;  // left when promoted (destroyed with the lane)
+    };
+    std::vector<std::unique_ptr<Lane>> lanes;
+    int prio_least = 0, prio_greatest = 0;
 };
 
 namespace {
@@ -1069,6 +1155,11 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
     srv->budget = mem_budget;
     srv->st = (cudaStream_t)stream;
     srv->eng = std::make_unique<Engine>(D, srv->w, srv->s, srv->st);
+    srv->eng->own_host_buffers();
+    if (cudaDeviceGetStreamPriorityRange(&srv->prio_least, &srv->prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        srv->prio_least = srv->prio_greatest = 0;
+    }
     *out = srv.release();
     return PLAS_OK;
 }
@@ -1076,8 +1167,13 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
 extern "C" int plas_server_set_policy(plas_server* srv, int policy) {
     set_last_error("");
     if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
-    if (policy < PLAS_SERVE_FIFO_FILL || policy > PLAS_SERVE_ALL)
+    if (policy < PLAS_SERVE_FIFO_FILL || policy > PLAS_SERVE_CONCURRENT)
         return fail(PLAS_ERR_INVALID_ARG, "unknown policy %d", policy);
+    const bool lanes_now = srv->policy == PLAS_SERVE_CONCURRENT;
+    const bool lanes_next = policy == PLAS_SERVE_CONCURRENT;
+    if (lanes_now != lanes_next && (!srv->running.empty() || !srv->lanes.empty()))
+        return fail(PLAS_ERR_INVALID_ARG,
+                    "switching to or from the concurrent policy needs a server with nothing admitted");
     srv->policy = policy;
     return PLAS_OK;
 }
@@ -1110,6 +1206,157 @@ extern "C" int plas_server_submit(plas_server* srv, const plas_job* job, long lo
 // enqueued: it reads the state of the previous step's batch (one batch
 // behind, as plas_sort does), so the GPU always has a batch queued while the
 // host retires, admits and chooses.
+namespace {
+
+// PLAS_SERVE_CONCURRENT: every admitted request advances on its own stream
+// with its own one-grid engine (graph-replayed batches of sweeps, two batches
+// in flight, state read one batch behind), so requests progress at their own
+// pace.  The oldest admitted request runs on a stream of the highest
+// priority, the others at the lowest: the block scheduler gives the oldest
+// request's CTAs the SMs first, as the plain one-at-a-time path would, and
+// the younger requests fill the SMs it leaves idle (small grids and small
+// radii do not fill the GPU).  When the oldest finishes, the next oldest moves
+// to the high-priority stream.
+int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int* n_done) {
+    constexpr size_t kMaxLanes = 16;
+    const plas_schedule& s = srv->s;
+    const int k = sweeps > 0 ? sweeps : 1;
+    // cancellations
+    for (auto& ln : srv->lanes) {
+        Slot* sl = ln->sl.get();
+        if (!sl->cancel || ln->done) continue;
+        ln->eng->drop(sl);
+        cudaFreeAsync(sl->mem, ln->st);
+        sl->mem = nullptr;
+        srv->in_use -= sl->bytes;
+        PLAS_CUDA(cudaEventCreateWithFlags(&ln->done, cudaEventDisableTiming));
+        PLAS_CUDA(cudaEventRecord(ln->done, ln->st));
+    }
+    // admission: FIFO into free lanes while the budget allows
+    while (!srv->queue.empty() && srv->lanes.size() < kMaxLanes) {
+        Slot* sl = srv->queue.front().get();
+        if (srv->budget && srv->in_use + sl->bytes > srv->budget) break;
+        auto ln = std::make_unique<plas_server::Lane>();
+        sl->N = (long long)sl->job.H * sl->job.W;
+        sl->geo = build_geometry(srv->s, sl->job.H, sl->job.W);
+        sl->nlev = (int)sl->geo.lv.size();
+        plan_slot(sl, srv->D);
+        const bool head = srv->lanes.empty();
+        PLAS_CUDA(cudaStreamCreateWithPriority(&ln->st, cudaStreamNonBlocking,
+                                               head ? srv->prio_greatest : srv->prio_least));
+        ln->head = head;
+        // the request's inputs were written on the server's stream
+        cudaEvent_t ready = nullptr;
+        PLAS_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        PLAS_CUDA(cudaEventRecord(ready, srv->st));
+        PLAS_CUDA(cudaStreamWaitEvent(ln->st, ready, 0));
+        cudaEventDestroy(ready);
+        void* mem = nullptr;
+        if (dev_alloc(&mem, sl->bytes, ln->st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamDestroy(ln->st);
+            if (srv->lanes.empty()) return fail(PLAS_ERR_OOM, "workspace allocation failed");
+            break;
+        }
+        sl->mem = (char*)mem;
+        sl->owns = true;
+        srv->in_use += sl->bytes;
+        ln->eng = std::make_unique<Engine>(srv->D, srv->w, srv->s, ln->st);
+        ln->eng->own_host_buffers();
+        if (int e = ln->eng->admit(sl)) return e;
+        ln->sl = std::move(srv->queue.front());
+        srv->queue.pop_front();
+        srv->lanes.push_back(std::move(ln));
+    }
+    // feed every lane up to two batches; consume landed read-backs
+    bool progress = false;
+    for (auto& lp : srv->lanes) {
+        plas_server::Lane& ln = *lp;
+        if (ln.done) continue;
+        Slot* sl = ln.sl.get();
+        if (ln.inflight > 0 && ln.eng->poll_ready(ln.buf ^ (ln.inflight == 2 ? 0 : 1))) {
+            const int oldest = ln.inflight == 2 ? ln.buf : ln.buf ^ 1;
+            if (int e = ln.eng->wait(oldest)) return e;
+            ln.inflight -= 1;
+            progress = true;
+            if (finished(*sl, s)) {
+                if (int e = ln.eng->retire(sl)) return e;
+                cudaFreeAsync(sl->mem, ln.st);
+                sl->mem = nullptr;
+                srv->in_use -= sl->bytes;
+                PLAS_CUDA(cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming));
+                PLAS_CUDA(cudaEventRecord(ln.done, ln.st));
+                continue;
+            }
+        }
+        while (ln.inflight < 2) {
+            if (int e = ln.eng->sweeps(k)) return e;
+            if (int e = ln.eng->poll(ln.buf)) return e;
+            ln.buf ^= 1;
+            ln.inflight += 1;
+            progress = true;
+        }
+    }
+    // completions (a lane's stream has finished its outputs)
+    for (size_t i = 0; i < srv->lanes.size();) {
+        plas_server::Lane& ln = *srv->lanes[i];
+        if (!ln.done) {
+            ++i;
+            continue;
+        }
+        const cudaError_t q = cudaEventQuery(ln.done);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (q != cudaSuccess) return fail(PLAS_ERR_CUDA, "output copies failed: %s", cudaGetErrorString(q));
+        Slot* sl = ln.sl.get();
+        if (!sl->cancel) {
+            if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
+            srv->completed.push_back(sl->job.ticket);
+        }
+        cudaEventDestroy(ln.done);
+        ln.eng.reset();
+        cudaStreamDestroy(ln.st);
+        for (cudaStream_t o : ln.old_streams) cudaStreamDestroy(o);
+        srv->lanes.erase(srv->lanes.begin() + i);
+        progress = true;
+    }
+    // the oldest unfinished request takes the high-priority stream
+    for (auto& lp : srv->lanes) {
+        if (lp->done) continue;
+        if (!lp->head) {
+            cudaStream_t hs = nullptr;
+            PLAS_CUDA(cudaStreamCreateWithPriority(&hs, cudaStreamNonBlocking, srv->prio_greatest));
+            if (int e = lp->eng->move_to_stream(hs)) return e;
+            lp->old_streams.push_back(lp->st);
+            lp->st = hs;
+            lp->head = true;
+        }
+        break;
+    }
+    // nothing moved: wait for the oldest read-back rather than spin
+    if (!progress) {
+        for (auto& lp : srv->lanes) {
+            if (lp->done) {
+                cudaEventSynchronize(lp->done);
+                break;
+            }
+            if (lp->inflight > 0) {
+                lp->eng->sync_poll(lp->inflight == 2 ? lp->buf : lp->buf ^ 1);
+                break;
+            }
+        }
+    }
+    const int n = std::min<int>(cap, (int)srv->completed.size());
+    for (int i = 0; i < n; ++i) done[i] = srv->completed[i];
+    srv->completed.erase(srv->completed.begin(), srv->completed.begin() + n);
+    *n_done = n;
+    return PLAS_OK;
+}
+
+}  // namespace
+
 extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, int cap,
                                 int* n_done) {
     set_last_error("");
@@ -1117,6 +1364,7 @@ extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, i
         return fail(PLAS_ERR_INVALID_ARG, "bad arguments");
     *n_done = 0;
     srv->step_no += 1;
+    if (srv->policy == PLAS_SERVE_CONCURRENT) return step_concurrent(srv, sweeps, done, cap, n_done);
     Engine& eng = *srv->eng;
     // cancelled requests leave the sweeps; their memory is released after
     // the work already queued on them, and their host records are kept while
@@ -1139,7 +1387,7 @@ extern "C" int plas_server_step(plas_server* srv, int sweeps, long long* done, i
         Slot* sl = srv->queue.front().get();
         if (srv->budget && srv->in_use + sl->bytes > srv->budget) break;
         void* mem = nullptr;
-        if (cudaMallocAsync(&mem, sl->bytes, srv->st) != cudaSuccess) {
+        if (dev_alloc(&mem, sl->bytes, srv->st) != cudaSuccess) {
             cudaGetLastError();
             if (srv->running.empty()) return fail(PLAS_ERR_OOM, "workspace allocation failed");
             break;  // wait for running requests to release memory
@@ -1234,13 +1482,20 @@ extern "C" int plas_server_cancel(plas_server* srv, long long ticket) {
             p->cancel = true;
             return PLAS_OK;
         }
+    for (auto& ln : srv->lanes)
+        if (ln->sl->job.ticket == ticket) {
+            if (ln->done || ln->sl->cancel)
+                return fail(PLAS_ERR_INVALID_ARG, "request %lld has finished or was cancelled", ticket);
+            ln->sl->cancel = true;
+            return PLAS_OK;
+        }
     return fail(PLAS_ERR_INVALID_ARG, "request %lld is not queued or running", ticket);
 }
 
 extern "C" int plas_server_status(plas_server* srv, int* queued, int* active, size_t* mem_in_use) {
     if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
     if (queued) *queued = (int)srv->queue.size();
-    if (active) *active = (int)srv->running.size();
+    if (active) *active = (int)(srv->running.size() + srv->lanes.size());
     if (mem_in_use) *mem_in_use = srv->in_use;
     return PLAS_OK;
 }
@@ -1248,6 +1503,16 @@ extern "C" int plas_server_status(plas_server* srv, int* queued, int* active, si
 extern "C" int plas_server_destroy(plas_server* srv) {
     if (!srv) return PLAS_OK;
     cudaStreamSynchronize(srv->st);
+    for (auto& ln : srv->lanes) {
+        cudaStreamSynchronize(ln->st);
+        if (ln->sl->owns && ln->sl->mem) cudaFreeAsync(ln->sl->mem, ln->st);
+        cudaStreamSynchronize(ln->st);
+        if (ln->done) cudaEventDestroy(ln->done);
+        ln->eng.reset();
+        cudaStreamDestroy(ln->st);
+        for (cudaStream_t o : ln->old_streams) cudaStreamDestroy(o);
+    }
+    srv->lanes.clear();
     for (auto& sl : srv->running)
         if (sl->owns && sl->mem) cudaFreeAsync(sl->mem, srv->st);
     for (auto& r : srv->retiring) cudaEventDestroy(r.ev);

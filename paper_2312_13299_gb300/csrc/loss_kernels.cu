@@ -36,6 +36,10 @@
 #include "../../include/plas.h"
 #include "plas_kernels.h"
 
+namespace plas {
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);  // plas_api.cu
+}
+
 namespace plas_loss {
 
 constexpr int kTX = 32;       // cells per strip
@@ -605,7 +609,7 @@ int plas_smooth_loss_fwd_ex(const float* x, int H, int W, int C, float sigma, in
             plas::set_last_error("workspace too small or misaligned");
             return PLAS_ERR_INVALID_ARG;
         }
-    } else if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+    } else if (plas::dev_alloc(&mem, need, st) != cudaSuccess) {
         cudaGetLastError();
         plas::set_last_error("allocation failed");
         return PLAS_ERR_OOM;
@@ -648,7 +652,7 @@ int plas_smooth_loss_bwd_ex(const float* x, int H, int W, int C, float sigma, in
             plas::set_last_error("workspace too small or misaligned");
             return PLAS_ERR_INVALID_ARG;
         }
-    } else if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+    } else if (plas::dev_alloc(&mem, need, st) != cudaSuccess) {
         cudaGetLastError();
         plas::set_last_error("allocation failed");
         return PLAS_ERR_OOM;

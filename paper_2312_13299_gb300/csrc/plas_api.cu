@@ -3,6 +3,7 @@
 // defaults, level count, row gather, the standalone target / grouping /
 // Philox entry points used for per-step parity, and grid metrics.  The sort
 // itself (single, batched and served) lives in engine.cu.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -22,6 +23,30 @@ namespace plas {
 static thread_local std::string g_last_error;
 
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+std::atomic<long long> g_alloc_fail_at{0};  // 0: none; n: the n-th allocation from now fails
+std::atomic<long long> g_stall_polls{0};    // read-backs still to be frozen
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    long long n = g_alloc_fail_at.load();
+    while (n > 0) {
+        if (g_alloc_fail_at.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
+bool injected_stall() {
+    long long n = g_stall_polls.load();
+    while (n > 0)
+        if (g_stall_polls.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -121,6 +146,7 @@ Geometry build_geometry(const plas_schedule& s, int H, int W) {
         const double sigma = s.sigma_ratio * phi;
         padded_tap_pairs(d.r, W - 1, sigma, &d.rx, &d.rpx, &d.ntpx, tx);
         padded_tap_pairs(d.r, H - 1, sigma, &d.ry, &d.rpy, &d.ntpy, ty);
+        g.max_steps = std::max({g.max_steps, d.ntpx, d.ntpy});
         d.off_tx = (long long)off; off += align_up((size_t)2 * d.ntpx, 4);
         d.off_ty = (long long)off; off += align_up((size_t)2 * d.ntpy, 4);
         // border norms, then their reciprocals, per axis
@@ -153,7 +179,7 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
     w.ref = (GridRef*)take(sizeof(GridRef));
     w.G = (float*)take(sizeof(float) * (size_t)N * grid_stride(D));
     w.T = (float*)take(sizeof(float) * (size_t)N * target_stride(D));
-    w.H1 = (float*)take(sizeof(float) * (size_t)N * D);
+    w.H1 = (float*)take(sizeof(float) * (size_t)W * h1_stride(H, D));
     w.pi = (uint32_t*)take(sizeof(uint32_t) * (size_t)std::max<long long>(N, 4));
     w.lv = (LevelDesc*)take(sizeof(LevelDesc) * (size_t)nlev);
     w.table = (float*)take(sizeof(float) * table_floats);
@@ -259,6 +285,28 @@ extern "C" {
 
 int plas_version(void) { return 200; }
 
+// Host-side fault injection.  kind 0 clears everything; kind 1 makes the
+// count-th device allocation from now on fail (count >= 1); kind 2 freezes
+// the next count state read-backs of the sweep engine, so that its progress
+// check sees a grid that does not advance.
+int plas_debug_inject(int kind, long long count) {
+    if (kind == 0) {
+        plas::g_alloc_fail_at.store(0);
+        plas::g_stall_polls.store(0);
+        return PLAS_OK;
+    }
+    if (count < 1) return plas::fail(PLAS_ERR_INVALID_ARG, "count must be >= 1");
+    if (kind == 1) {
+        plas::g_alloc_fail_at.store(count);
+        return PLAS_OK;
+    }
+    if (kind == 2) {
+        plas::g_stall_polls.store(count);
+        return PLAS_OK;
+    }
+    return plas::fail(PLAS_ERR_INVALID_ARG, "unknown injection kind %d", kind);
+}
+
 int plas_set_tuning(int H, int W, int D, const plas_tuning* t) {
     set_last_error("");
     if (H < 1 || W < 1 || !channels_supported(D)) return fail(PLAS_ERR_INVALID_ARG, "bad shape");
@@ -275,6 +323,7 @@ int plas_set_tuning(int H, int W, int D, const plas_tuning* t) {
     tu.small_below = t->fir_small_below;
     tu.medium_below = t->fir_medium_below;
     tu.assign_per_sm = t->assign_ctas_per_sm;
+    tu.large_tma = t->large_tma ? 1 : 0;
     install_tuning(H, W, D, &tu);
     return PLAS_OK;
 }
@@ -288,6 +337,7 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out) {
     out->fir_small_below = t.small_below;
     out->fir_medium_below = t.medium_below;
     out->assign_ctas_per_sm = t.assign_per_sm;
+    out->large_tma = t.large_tma;
     return PLAS_OK;
 }
 
@@ -388,7 +438,7 @@ static int target_impl(const float* x, int H, int W, int D, const float* weights
     Workspace ws{};
     const size_t need = workspace_layout(H, W, D, 1, g.table_floats, nullptr, nullptr, mode == 1);
     void* mem = nullptr;
-    if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+    if (dev_alloc(&mem, need, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(PLAS_ERR_OOM, "workspace allocation failed");
     }
@@ -419,9 +469,12 @@ static int target_impl(const float* x, int H, int W, int D, const float* weights
         if (mode == 1) {
             launch_box_target(ws.ref, H, W, D, num_sms(), st);
         } else {
-            const int var = fir_tiling(g.lv[0].r, tuning_for(H, W, D));
-            launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st);
-            launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st);
+            const Tuning tu = tuning_for(H, W, D);
+            const int var = fir_tiling(g.lv[0].r, tu);
+            FirTma tma;
+            if (tu.large_tma) make_fir_tma(ws.G, ws.H1, H, W, D, g.max_steps, &tma);
+            launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st, &tma);
+            launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st, &tma);
         }
         launch_copy_features(ws.T, (int)N, D, target_stride(D), T, st);
         rc = check_launch("target");
@@ -475,7 +528,7 @@ int plas_check_permutation(const int32_t* perm, int N, int* first_bad, void* str
     const size_t words = ((size_t)N + 31) / 32;
     const size_t bytes = 16 + 2 * words * sizeof(uint32_t);
     char* mem = nullptr;
-    if (cudaMallocAsync((void**)&mem, bytes, st) != cudaSuccess) {
+    if (dev_alloc((void**)&mem, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(PLAS_ERR_OOM, "allocation failed");
     }
@@ -509,7 +562,7 @@ int plas_grid_metrics(const float* grid, int H, int W, int D, double scale, doub
     if (H < 1 || W < 1 || D < 1 || !grid || !out) return fail(PLAS_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     double* acc = nullptr;
-    if (cudaMallocAsync((void**)&acc, sizeof(double) * 3, st) != cudaSuccess) {
+    if (dev_alloc((void**)&acc, sizeof(double) * 3, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(PLAS_ERR_OOM, "allocation failed");
     }

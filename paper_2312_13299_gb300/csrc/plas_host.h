@@ -14,6 +14,13 @@ namespace plas {
 
 // ---- errors -------------------------------------------------------------------
 int fail(int code, const char* fmt, ...);
+
+// ---- host-side fault injection (plas_debug_inject; tests only) -----------------
+// Every device allocation of the library goes through dev_alloc, which fails
+// with cudaErrorMemoryAllocation when an injected failure is due.  A frozen
+// read-back makes the progress check see no advance.  Neither touches the GPU.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+bool injected_stall();
 int check_launch(const char* what);
 int num_sms();
 
@@ -43,6 +50,7 @@ inline bool grid_fits(long long H, long long W, int D) {
 // (2 sigma^2)) in FP64, stored twice each (pairs for the packed FMA).
 struct Geometry {
     std::vector<LevelDesc> lv;
+    int max_steps = 0;  // largest padded tap-step count of any level and pass
     std::vector<float> table;  // padded tap pairs per level (norms filled on the device)
     size_t table_floats = 0;
 };
@@ -79,6 +87,7 @@ struct Tuning {
     int small_below = kDefaultSmallBelow;    // direct FIR kernel (no ring) below this radius
     int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row
     int assign_per_sm = kDefaultAssignPerSm;
+    int large_tma = 1;  // the large tiling streams rows with tensor copies where a grid allows
 };
 inline int fir_tiling(int r, const Tuning& t) {
     return r < t.small_below ? kFirSmallRadius : r < t.medium_below ? kFirMediumRadius : kFirLargeRadius;

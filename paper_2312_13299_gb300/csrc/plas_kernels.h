@@ -21,6 +21,25 @@ constexpr int kFirX = 8;       // outputs per lane and column of the FIR passes
 constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
 // FIR tilings (identical results); which one a radius uses is a tuning choice
 constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1, kFirMediumRadius = 2, kFirTilings = 3;
+
+// Row stride (floats) of the first-pass output H1 ([x][y][d], W rows of H*D
+// values): padded to 16 bytes so that tensor copies can stream its rows.
+__host__ __device__ inline int h1_stride(int H, int D) { return (H * D + 3) & ~3; }
+
+// The large tiling's persistent tensor-copy kernel (single grids, even D):
+// per grid, a tensor map of G (pass 0, [H][W][gs] floats) and of H1 (pass 1,
+// [W][h1_stride] floats), the shared-memory row size of each pass and the
+// tap steps kept resident.  ok = false: the chunked ring kernel runs instead.
+struct FirTma {
+    alignas(64) unsigned char map[2][128];  // CUtensorMap per pass
+    int rowf[2];    // floats per ring row (pass 0: ncell * gs, pass 1: 128)
+    int ncell;      // cells per pass-0 row box
+    int steps;      // tap steps kept in shared memory (>= every level's)
+    bool ok = false;
+};
+// Builds *t for a grid whose G and H1 live at the given addresses; max_steps
+// = the largest padded tap-step count of any level.  false: not eligible.
+bool make_fir_tma(const float* G, const float* H1, int H, int W, int D, int max_steps, FirTma* t);
 constexpr int kAssignThreads = 256;
 
 struct Weights {
@@ -124,7 +143,7 @@ void launch_norms(const LevelDesc* lv_dev, int nlev, int H, int W, float* table,
 // device; launch_fir calls it too, but a stream capture calls it first)
 void prepare_fir_launches();
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
-                cudaStream_t s);
+                cudaStream_t s, const FirTma* tma = nullptr);
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
                    cudaStream_t s);
 

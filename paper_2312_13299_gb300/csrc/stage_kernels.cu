@@ -337,7 +337,7 @@ extern "C" int plas_grid_select(const float* opacity, long long N, int stride, i
     void* mem = workspace;
     if (mem) {
         if (ws_bytes < need || !aligned(mem, 256)) return fail(PLAS_ERR_INVALID_ARG, "workspace too small or misaligned");
-    } else if (cudaMallocAsync(&mem, need, st) != cudaSuccess) {
+    } else if (plas::dev_alloc(&mem, need, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(PLAS_ERR_OOM, "grid-select workspace");
     }

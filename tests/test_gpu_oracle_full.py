@@ -84,15 +84,21 @@ def _check(res, case):
         assert res.state[k] == getattr(ws, k), k
 
 
-def test_full_sort_3dgs_512_matches_oracle_fixture(plas):
-    """The 512 x 512 x 14 + 45 workload end to end: permutation, carried
-    attributes, every iteration's residual sum and the iterations per level
-    equal the complete oracle run's; the objectives agree within 1e-4."""
-    fx = _fixture("3dgs-512")
-    x, c = synth.gaussians_3dgs(512 * 512, seed=0)
+@pytest.mark.parametrize("name,side", [("3dgs-512", 512), ("3dgs-1024", 1024)])
+def test_full_sort_matches_oracle_fixture(plas, name, side):
+    """The 512 x 512 and 1024 x 1024 (x 14 + 45) workloads end to end, with
+    the launch shapes the benchmark tunes: permutation, carried attributes,
+    every iteration's residual sum and the iterations per level equal the
+    complete oracle run's; the objectives agree within 1e-4."""
+    fx = _fixture(name)
+    x, c = synth.gaussians_3dgs(side * side, seed=0)
     xc = torch.from_numpy(x).cuda()
-    r = plas.sort(xc, 512, 512, carried=torch.from_numpy(c).cuda(), seed=0, want_sorted=True,
-                  trace_cap=1 << 17)
+    plas.autotune(side, side, 14)
+    try:
+        r = plas.sort(xc, side, side, carried=torch.from_numpy(c).cuda(), seed=0, want_sorted=True,
+                      trace_cap=1 << 17)
+    finally:
+        plas.set_tuning(side, side, 14)
     assert r.state["it"] == fx["iterations"]
     assert _sha(r.perm, "<i4") == fx["sha256_perm_int32"]
     assert _sha(r.carried, "<f4") == fx["sha256_carried_out_float32"]
@@ -101,7 +107,7 @@ def test_full_sort_3dgs_512_matches_oracle_fixture(plas):
     per_level = np.bincount(r.trace_level.cpu().numpy(), minlength=fx["levels"])
     assert per_level.tolist() == fx["iterations_per_level"]
     assert r.state["d_last"] == float.fromhex(fx["final_state"]["d_last"])
-    nl2, _, _ = plas.grid_metrics(r.sorted.reshape(512, 512, -1), 1.0)
+    nl2, _, _ = plas.grid_metrics(r.sorted.reshape(side, side, -1), 1.0)
     assert abs(nl2 - fx["mean_neighbour_l2"]) <= 1e-4 * fx["mean_neighbour_l2"]
     assert abs(r.state["d_last"] - fx["mean_l2_to_target"]) <= 1e-4 * fx["mean_l2_to_target"]
 
@@ -112,7 +118,7 @@ def test_batch_sort_matches_oracle(plas, cases):
         _check(res, case)
 
 
-@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all"])
+@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent"])
 def test_server_matches_oracle(plas, cases, policy):
     """Three requests first, the others (the 512 x 512 one last) arriving
     while those run; every result equals the oracle's."""

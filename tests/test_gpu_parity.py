@@ -75,23 +75,30 @@ def test_target_bitexact_wide_magnitudes(plas, orc, phi):
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
-# tuning that forces one FIR tiling at every radius: (small_below, medium_below)
-_TILINGS = {"direct": (10 ** 6, 10 ** 6), "64-row": (0, 10 ** 6), "128-row": (0, 0)}
+# tuning that forces one FIR tiling at every radius: (small_below,
+# medium_below, large_tma)
+_TILINGS = {"direct": (10 ** 6, 10 ** 6, 0), "64-row": (0, 10 ** 6, 0), "128-row": (0, 0, 0),
+            "128-row-tensor-copy": (0, 0, 1)}
 
 
 @pytest.mark.parametrize("tiling", sorted(_TILINGS))
 @pytest.mark.parametrize("H,W,D,phi", [(200, 136, 14, 60.0), (131, 77, 5, 30.0), (96, 160, 3, 6.0),
-                                       (1, 300, 14, 40.0), (257, 1, 2, 70.0), (68, 52, 64, 20.0)])
+                                       (1, 300, 14, 40.0), (257, 1, 2, 70.0), (68, 52, 64, 20.0),
+                                       (300, 290, 14, 140.0), (150, 133, 6, 33.0),
+                                       (129, 140, 10, 50.0), (77, 300, 12, 25.0), (260, 70, 16, 90.0)])
 def test_target_bitexact_every_tiling(plas, orc, tiling, H, W, D, phi):
-    """Each FIR tiling (the direct kernel, or the ring kernel with 64 or 128
-    rows per CTA) gives the oracle's target bit for bit, on ragged grids
-    whose sides and column counts span several tiles with partial ones at the
-    end, and on single-row/column grids."""
+    """Each FIR tiling (the direct kernel, the ring kernel with 64 or 128 rows
+    per CTA, and the persistent 128-row kernel that streams rows with tensor
+    copies, for even D) gives the oracle's target bit for bit, on ragged
+    grids whose sides and column counts span several tiles with partial ones
+    at the end (more tiles than SMs for the persistent kernel), and on
+    single-row/column grids."""
     rng = np.random.default_rng(H * 7 + W * 3 + D)
     x = rng.random((H * W, D), dtype=np.float32)
     perm = rng.permutation(H * W).astype(np.int32)
-    sb, mb = _TILINGS[tiling]
-    plas.set_tuning(H, W, D, fir_small_below=sb, fir_medium_below=mb, assign_ctas_per_sm=8)
+    sb, mb, tma = _TILINGS[tiling]
+    plas.set_tuning(H, W, D, fir_small_below=sb, fir_medium_below=mb, assign_ctas_per_sm=8,
+                    large_tma=tma)
     try:
         got = plas.target(_cuda(x), H, W, _cuda(perm), phi).cpu().numpy()
     finally:
@@ -193,7 +200,7 @@ def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
     any installed choice (always 128-row, always 64-row, always direct, a
     mix by radius, 1 or 16 assignment CTAs per SM) gives the oracle's
     permutation and schedule trace."""
-    H, W, D = 72, 56, 5
+    H, W, D = 72, 56, 6
     t = plas.autotune(H, W, D)
     assert t["radius"][0] == 1 and len(t["fir_small_us"]) == len(t["radius"])
     assert len(t["fir_medium_us"]) == len(t["radius"])
@@ -201,16 +208,19 @@ def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
     assert all((v > 0) == (r <= 32) for v, r in zip(t["fir_small_us"], t["radius"]))
     assert t["fir_small_below"] <= t["fir_medium_below"]
     assert t["assign_ctas_per_sm"] in t["assign_per_sm"]
+    assert all(v > 0 for v in t["fir_large_tma_us"] + t["fir_large_ring_us"])  # D = 6 is eligible
     rng = np.random.default_rng(11)
     x = rng.random((H * W, D), dtype=np.float32)
     want = orc.sort(x, H, W, seed=11)
     xc = _cuda(x)
     try:
-        for small_below, medium_below, per_sm in [(0, 0, 1), (10 ** 6, 10 ** 6, 16), (0, 10 ** 6, 2),
-                                                  (3, 12, 8),
-                                                  (t["fir_small_below"], t["fir_medium_below"], 4)]:
+        for small_below, medium_below, per_sm, tma in [(0, 0, 1, 0), (0, 0, 2, 1),
+                                                       (10 ** 6, 10 ** 6, 16, 1), (0, 10 ** 6, 2, 0),
+                                                       (3, 12, 8, 1),
+                                                       (t["fir_small_below"], t["fir_medium_below"], 4,
+                                                        t["large_tma"])]:
             plas.set_tuning(H, W, D, fir_small_below=small_below, fir_medium_below=medium_below,
-                            assign_ctas_per_sm=per_sm)
+                            assign_ctas_per_sm=per_sm, large_tma=tma)
             got = plas.sort(xc, H, W, seed=11, trace_cap=1 << 14)
             assert np.array_equal(got.perm.cpu().numpy(), want["perm"]), (small_below, medium_below,
                                                                           per_sm)

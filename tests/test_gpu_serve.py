@@ -53,7 +53,7 @@ def test_batch_sort_d3(plas):
         assert torch.equal(got.perm, one.perm) and got.state["it"] == one.state["it"]
 
 
-@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all"])
+@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent"])
 def test_server_arrivals_while_running(plas, policy):
     reqs = _requests(seed0=10)
     srv = plas.Server(14, policy=policy)
@@ -108,13 +108,14 @@ def test_server_rejects_request_over_budget(plas):
     srv.close()
 
 
-def test_server_cancel_queued_and_running(plas):
+@pytest.mark.parametrize("policy", ["all", "concurrent"])
+def test_server_cancel_queued_and_running(plas, policy):
     """A request cancelled while queued and one cancelled while running are
     never reported; the others give exactly their results alone, and the
     server ends with nothing queued, admitted or allocated.  Unknown,
     finished and repeated cancellations are rejected."""
     reqs = _requests(seed0=30)[:4]
-    srv = plas.Server(14, policy="all")
+    srv = plas.Server(14, policy=policy)
     t = [srv.submit(r["x"], r["H"], r["W"], r["carried"], r["seed"]) for r in reqs]
     srv.cancel(t[2])  # still queued: nothing is admitted before the first step
     with pytest.raises(RuntimeError):
@@ -164,3 +165,24 @@ def test_server_cancel_frees_budget_for_the_next_request(plas):
     _same(results[ts], _alone(plas, small))
     assert srv.status() == (0, 0, 0)
     srv.close()
+
+
+def test_server_policy_switch_needs_an_idle_server(plas):
+    """The concurrent policy keeps its requests on lanes of their own, so a
+    switch to or from it is refused while anything is admitted."""
+    reqs = _requests(seed0=60)[:2]
+    srv = plas.Server(14, policy="all")
+    t = srv.submit(reqs[0]["x"], reqs[0]["H"], reqs[0]["W"], reqs[0]["carried"], reqs[0]["seed"])
+    srv.step(sweeps=2)
+    with pytest.raises(RuntimeError):
+        srv._lib_policy("concurrent")
+    results = {}
+    while t not in results:
+        results.update(srv.step(sweeps=8))
+    srv._lib_policy("concurrent")
+    t2 = srv.submit(reqs[1]["x"], reqs[1]["H"], reqs[1]["W"], reqs[1]["carried"], reqs[1]["seed"])
+    while t2 not in results:
+        results.update(srv.step(sweeps=8))
+    srv.close()
+    _same(results[t], _alone(plas, reqs[0]))
+    _same(results[t2], _alone(plas, reqs[1]))
