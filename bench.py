@@ -826,7 +826,7 @@ def main():
                     "(poisson = 0.8 x plain capacity, overload = 1.25 x, burst)")
     ap.add_argument("--no-serve", dest="serve_in_bench", action="store_false",
                     help="leave the served-stream comparison out of the default line")
-    ap.add_argument("--serve-policy", default="all",
+    ap.add_argument("--serve-policy", default="adaptive",
                     help="server policies of the default line's served-stream comparison")
     args = ap.parse_args()
     if args.ncu_case > 0:

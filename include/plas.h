@@ -85,6 +85,18 @@ typedef struct plas_schedule {
                         /* T = ((float)S / (float)n) * 2^-s.  Its cost does  */
                         /* not grow with r (summed-area tables).  Single     */
                         /* sorts only (plas_sort, plas_target_box).          */
+    int persistent;     /* 1: one cooperative launch per batch of           */
+                        /* iters_per_poll iterations of every grid of a      */
+                        /* sweep (grid-wide barriers between the phases,     */
+                        /* bounded waits); 0 (default) or -1: separate       */
+                        /* launches per kernel class, graph-replayed (faster */
+                        /* in every configuration measured).  Gaussian       */
+                        /* target only.  Identical results either way.  A    */
+                        /* persistent launch holds up to every SM; sorts on  */
+                        /* other streams at the same time may delay it, and  */
+                        /* a barrier that waits 2 s gives up with            */
+                        /* PLAS_ERR_TIMEOUT (the GPU stays usable).  The     */
+                        /* concurrent server policy never uses it.           */
     long long* trace_S; /* device or NULL: trace_S[it] = fixed-point residual */
                         /* sum of iteration it (mean L2 distance * N * 2^k)  */
     int* trace_level;   /* device or NULL: level of iteration it             */
@@ -556,6 +568,8 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out);
  *     the next oldest is moved to a high-priority stream.  A step feeds
  *     every lane and waits only when no lane can move.  Switching to or from
  *     this policy needs a server with nothing admitted.
+ *   PLAS_SERVE_ADAPTIVE: FIFO_FILL while fewer than eight requests are
+ *     admitted, ALL under a larger backlog.
  *   PLAS_ERR_INVALID_ARG for an unknown policy.
  * plas_server_cancel: withdraws a request that is queued or running.  A
  *   queued request is removed at once; a running one leaves the sweeps at
@@ -575,7 +589,7 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out);
  */
 typedef struct plas_server plas_server;
 enum { PLAS_SERVE_FIFO_FILL = 0, PLAS_SERVE_SHORTEST_FIRST = 1, PLAS_SERVE_ALL = 2,
-       PLAS_SERVE_CONCURRENT = 3 };
+       PLAS_SERVE_CONCURRENT = 3, PLAS_SERVE_ADAPTIVE = 4 };
 int plas_server_create(int D, const float* weights, const plas_schedule* sched,
                        size_t mem_budget, void* stream, plas_server** out);
 int plas_server_set_policy(plas_server* srv, int policy);
@@ -600,7 +614,11 @@ const char* plas_last_error(void);  /* thread-local; "" if none */
  *           what it had allocated;
  *   kind 2: the sweep engine's next count state read-backs are frozen (the
  *           host keeps its previous copy), so its progress check sees grids
- *           that do not advance and the call returns PLAS_ERR_INTERNAL.
+ *           that do not advance and the call returns PLAS_ERR_INTERNAL;
+ *   kind 3: the next count persistent sweep launches (plas_schedule.
+ *           persistent) get a zero wait limit at their grid-wide barriers:
+ *           the first wait gives up at once, the launch ends early and the
+ *           call returns PLAS_ERR_TIMEOUT (the GPU stays usable).
  * Process-wide (all threads).  Returns PLAS_OK or PLAS_ERR_INVALID_ARG
  * (unknown kind, count < 1).
  */

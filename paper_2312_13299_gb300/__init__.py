@@ -46,6 +46,7 @@ class Schedule:
     profile: bool = False
     graphs: bool = True
     target_mode: int = 0  # 0 Gaussian target, 1 box target (fast low-pass variant)
+    persistent: int = 0   # 1: one cooperative launch per batch of sweeps; 0 / -1: graph-replayed launches
 
     def to_c(self, trace_S: Optional[torch.Tensor] = None,
              trace_level: Optional[torch.Tensor] = None) -> _lib.plas_schedule:
@@ -56,6 +57,7 @@ class Schedule:
         s.iters_per_poll, s.max_iters, s.profile = self.iters_per_poll, self.max_iters, int(self.profile)
         s.graphs = int(self.graphs)
         s.target_mode = int(self.target_mode)
+        s.persistent = int(self.persistent)
         s.trace_S = trace_S.data_ptr() if trace_S is not None else None
         s.trace_level = trace_level.data_ptr() if trace_level is not None else None
         cap = 0
@@ -325,10 +327,10 @@ class Server:
     sort() of each request alone under every policy.  All work runs on the
     stream current at construction."""
 
-    POLICIES = {"fifo_fill": 0, "shortest_first": 1, "all": 2, "concurrent": 3}
+    POLICIES = {"fifo_fill": 0, "shortest_first": 1, "all": 2, "concurrent": 3, "adaptive": 4}
 
     def __init__(self, D: int, weights=None, schedule: Optional[Schedule] = None,
-                 mem_budget: int = 0, device=None, policy: str = "fifo_fill"):
+                 mem_budget: int = 0, device=None, policy: Optional[str] = None):
         self._lib = load()
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
@@ -345,6 +347,8 @@ class Server:
         self._live = {}
         self._cancelled = []  # (step number, tensors) kept until that step's work has run
         self._steps = 0
+        if policy is None:  # the box target is served by one lane per request
+            policy = "concurrent" if (schedule and schedule.target_mode == 1) else "fifo_fill"
         if policy not in self.POLICIES:
             self.close()
             raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")

@@ -229,6 +229,26 @@ class Engine {
             p.ctas[kClsFirY] = fir_ctas(sl->job.H, sl->job.W * D_, p.var);
             p.ctas[kClsFirX] = fir_ctas(sl->job.W, sl->job.H * D_, p.var);
         }
+        if (one) persist_ = want_persist();
+        if (persist_) {
+            // one cooperative launch for the k sweeps: the work items of each
+            // phase are the medium tiling's FIR tiles and the assignment slices
+            const int ny = one ? fir_ctas(active_[0]->job.H, active_[0]->job.W * D_, kFirMediumRadius)
+                               : total_[kClsFirY];
+            const int nx = one ? fir_ctas(active_[0]->job.W, active_[0]->job.H * D_, kFirMediumRadius)
+                               : total_[kClsFirX];
+            const int rc = launch_persist(p.grids, (int)active_.size(), p.map[kClsFirY], ny,
+                                          p.map[kClsFirX], nx, p.map[kClsAssign], p.ctas[kClsAssign], D_,
+                                          k, s_.tol, active_[0]->ws.pctl, persist_wait_limit_ns(), st_);
+            launches_ += 1;
+            persist_launches_ += 1;
+            if (rc != 0) {
+                const cudaError_t e = cudaGetLastError();
+                return fail(rc == -1 ? PLAS_ERR_INVALID_ARG : PLAS_ERR_CUDA,
+                            "persistent sweep launch failed: %s", cudaGetErrorString(e));
+            }
+            return check_launch("persistent sweep");
+        }
         launches_ += (long long)k * kClsCount;
         if (s_.graphs && !s_.profile && !graphs_failed_) {
             // every kernel reads its grid's level from device state, so a batch
@@ -265,6 +285,13 @@ class Engine {
                                       cudaMemcpyDeviceToHost, st_));
         PLAS_CUDA(cudaEventRecord(ev_[buf], st_));
         return PLAS_OK;
+    }
+
+    // Whether the next sweeps run as one persistent cooperative launch (on
+    // request only: graph-replayed launches measured faster for every grid
+    // size and batch tried, so they stay the default).
+    bool want_persist() const {
+        return s_.persistent > 0 && s_.target_mode == 0 && !s_.profile;
     }
 
     // Whether poll 'buf' has landed (wait() then returns without blocking),
@@ -485,11 +512,18 @@ class Engine {
             r.target_mode = s_.target_mode;
             r.sat = sl->ws.sat;
         }
+        // the persistent sweep runs the medium FIR tiling, separate launches
+        // the large one
+        persist_ = want_persist();
+        const int fv = persist_ ? kFirMediumRadius : kFirLargeRadius;
         std::vector<CtaMap> maps;
         for (int c = 0; c < kClsCount; ++c) {
             total_[c] = 0;
             for (size_t i = 0; i < active_.size(); ++i) {
-                const int n = active_[i]->ctas[c];
+                const Job& j = active_[i]->job;
+                const int n = c == kClsFirY   ? fir_ctas(j.H, j.W * D_, fv)
+                              : c == kClsFirX ? fir_ctas(j.W, j.H * D_, fv)
+                                              : active_[i]->ctas[c];
                 for (int l = 0; l < n; ++l) maps.push_back(CtaMap{(int)i, l, n, 0});
                 total_[c] += n;
             }
@@ -545,6 +579,7 @@ class Engine {
     GridRef* dgrids_ = nullptr;
     CtaMap* dmap_[kClsCount] = {nullptr, nullptr, nullptr};
     int total_[kClsCount] = {0, 0, 0};
+    bool persist_ = false;  // the next sweeps run as one persistent launch
     char* host_ = nullptr;
     size_t host_cap_ = 0;
     char* polled_base_[2] = {nullptr, nullptr};
@@ -560,11 +595,14 @@ class Engine {
    public:
     long long captures_ = 0;
     long long graph_launches_ = 0;
+    long long persist_launches_ = 0;
 };
 
 int status_error(const DevState& st) {
     if (st.nonfinite) return fail(PLAS_ERR_NONFINITE, "sort input holds NaN or Inf");
     if (st.bad_index) return fail(PLAS_ERR_INVALID_ARG, "perm_init holds an index outside [0, N)");
+    if (st.status == PLAS_ERR_TIMEOUT)
+        return fail(PLAS_ERR_TIMEOUT, "a bounded device wait gave up (no progress for 2 s)");
     return fail(PLAS_ERR_INTERNAL, "device status %d", st.status);
 }
 
@@ -961,8 +999,11 @@ static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedul
         if (per_job) (*per_job)[i] = b;
         total += b;
         grids += 1;
-        ctas += fir_ctas(H, W * D, kFirLargeRadius) +
-                fir_ctas(W, H * D, kFirLargeRadius) + assign_ctas(H, W, nsm, kAssignMaxPerSm);
+        // CTA maps sized for the tiling with the most tiles (the medium one,
+        // which persistent sweeps run)
+        ctas += std::max(fir_ctas(H, W * D, kFirLargeRadius), fir_ctas(H, W * D, kFirMediumRadius)) +
+                std::max(fir_ctas(W, H * D, kFirLargeRadius), fir_ctas(W, H * D, kFirMediumRadius)) +
+                assign_ctas(H, W, nsm, kAssignMaxPerSm);
     }
     if (maps_at) *maps_at = total;
     return total + Engine::map_bytes(grids, ctas);
@@ -974,6 +1015,12 @@ extern "C" size_t plas_batch_workspace_bytes(int n, const plas_job* jobs, int D)
     plas_default_schedule(&s);
     return batch_bytes(n, jobs, D, s, nullptr, nullptr);
 }
+
+struct plas_server;
+namespace {
+int run_lane_batch(int n, const plas_job* jobs, int D, const Weights& w, const plas_schedule& s,
+                   char* base, const std::vector<size_t>& per, cudaStream_t st);
+}  // namespace
 
 extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
                                const plas_schedule* sched, void* workspace, size_t ws_bytes,
@@ -987,7 +1034,6 @@ extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* 
     s.trace_level = nullptr;
     s.trace_cap = 0;
     if (int e = validate_schedule(s)) return e;
-    if (s.target_mode != 0) return fail(PLAS_ERR_INVALID_ARG, "the box target is available for single sorts");
     Weights w{};
     if (int e = make_weights(weights, D, &w)) return e;
     for (int i = 0; i < n; ++i) {
@@ -1018,6 +1064,13 @@ extern "C" int plas_batch_sort(int n, const plas_job* jobs, int D, const float* 
         owns = true;
     }
     int rc = PLAS_OK;
+    if (s.target_mode == 1) {
+        // the box target: the inputs are ready on the caller's stream, each
+        // grid then runs on a lane of its own
+        rc = run_lane_batch(n, jobs, D, w, s, base, per, st);
+        if (owns) cudaFreeAsync(base, st);
+        return rc;
+    }
     {
         std::vector<std::unique_ptr<Slot>> slots;
         Engine eng(D, w, s, st);
@@ -1083,6 +1136,7 @@ struct plas_server {
     };
     std::vector<std::unique_ptr<Lane>> lanes;
     int prio_least = 0, prio_greatest = 0;
+    int first_error = 0;  // a lane's grid that ended with a device status
 };
 
 namespace {
@@ -1116,11 +1170,17 @@ int level_of(const Slot* sl) {
 // short to fill the GPU, share one).  ALL: every admitted grid.
 constexpr double kFillNs = 600000.0;
 
+// ADAPTIVE: FIFO_FILL while fewer than kBacklog requests are admitted (the
+// oldest request runs nearly alone, as on the plain path), ALL under a
+// backlog, where sweeping many grids together raises throughput.
+constexpr size_t kBacklog = 8;
+
 std::vector<Slot*> choose(plas_server* srv) {
     std::vector<Slot*> cand;
     for (auto& p : srv->running)
         if (p->active && !finished(*p, srv->s)) cand.push_back(p.get());
     if (srv->policy == PLAS_SERVE_ALL) return cand;
+    if (srv->policy == PLAS_SERVE_ADAPTIVE && cand.size() >= kBacklog) return cand;
     if (srv->policy == PLAS_SERVE_SHORTEST_FIRST)
         std::stable_sort(cand.begin(), cand.end(), [](const Slot* a, const Slot* b) {
             return a->rem_ns[level_of(a)] < b->rem_ns[level_of(b)];
@@ -1151,7 +1211,9 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
     srv->s.trace_level = nullptr;
     srv->s.trace_cap = 0;
     if (int e = validate_schedule(srv->s)) return e;
-    if (srv->s.target_mode != 0) return fail(PLAS_ERR_INVALID_ARG, "the box target is available for single sorts");
+    // the box target runs one grid per launch: its requests take the
+    // concurrent policy, one lane (stream + engine) each
+    if (srv->s.target_mode == 1) srv->policy = PLAS_SERVE_CONCURRENT;
     srv->budget = mem_budget;
     srv->st = (cudaStream_t)stream;
     srv->eng = std::make_unique<Engine>(D, srv->w, srv->s, srv->st);
@@ -1167,8 +1229,10 @@ extern "C" int plas_server_create(int D, const float* weights, const plas_schedu
 extern "C" int plas_server_set_policy(plas_server* srv, int policy) {
     set_last_error("");
     if (!srv) return fail(PLAS_ERR_INVALID_ARG, "NULL server");
-    if (policy < PLAS_SERVE_FIFO_FILL || policy > PLAS_SERVE_CONCURRENT)
+    if (policy < PLAS_SERVE_FIFO_FILL || policy > PLAS_SERVE_ADAPTIVE)
         return fail(PLAS_ERR_INVALID_ARG, "unknown policy %d", policy);
+    if (srv->s.target_mode == 1 && policy != PLAS_SERVE_CONCURRENT)
+        return fail(PLAS_ERR_INVALID_ARG, "the box target is served by the concurrent policy only");
     const bool lanes_now = srv->policy == PLAS_SERVE_CONCURRENT;
     const bool lanes_next = policy == PLAS_SERVE_CONCURRENT;
     if (lanes_now != lanes_next && (!srv->running.empty() || !srv->lanes.empty()))
@@ -1226,7 +1290,7 @@ int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int*
         Slot* sl = ln->sl.get();
         if (!sl->cancel || ln->done) continue;
         ln->eng->drop(sl);
-        cudaFreeAsync(sl->mem, ln->st);
+        if (sl->owns) cudaFreeAsync(sl->mem, ln->st);
         sl->mem = nullptr;
         srv->in_use -= sl->bytes;
         PLAS_CUDA(cudaEventCreateWithFlags(&ln->done, cudaEventDisableTiming));
@@ -1251,17 +1315,23 @@ int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int*
         PLAS_CUDA(cudaEventRecord(ready, srv->st));
         PLAS_CUDA(cudaStreamWaitEvent(ln->st, ready, 0));
         cudaEventDestroy(ready);
-        void* mem = nullptr;
-        if (dev_alloc(&mem, sl->bytes, ln->st) != cudaSuccess) {
-            cudaGetLastError();
-            cudaStreamDestroy(ln->st);
-            if (srv->lanes.empty()) return fail(PLAS_ERR_OOM, "workspace allocation failed");
-            break;
+        if (!sl->mem) {  // (a batch hands its requests carved workspaces)
+            void* mem = nullptr;
+            if (dev_alloc(&mem, sl->bytes, ln->st) != cudaSuccess) {
+                cudaGetLastError();
+                cudaStreamDestroy(ln->st);
+                if (srv->lanes.empty()) return fail(PLAS_ERR_OOM, "workspace allocation failed");
+                break;
+            }
+            sl->mem = (char*)mem;
+            sl->owns = true;
         }
-        sl->mem = (char*)mem;
-        sl->owns = true;
         srv->in_use += sl->bytes;
-        ln->eng = std::make_unique<Engine>(srv->D, srv->w, srv->s, ln->st);
+        // lanes run side by side: no cooperative launches (they would compete
+        // for co-residency)
+        plas_schedule ls = srv->s;
+        ls.persistent = -1;
+        ln->eng = std::make_unique<Engine>(srv->D, srv->w, ls, ln->st);
         ln->eng->own_host_buffers();
         if (int e = ln->eng->admit(sl)) return e;
         ln->sl = std::move(srv->queue.front());
@@ -1281,7 +1351,7 @@ int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int*
             progress = true;
             if (finished(*sl, s)) {
                 if (int e = ln.eng->retire(sl)) return e;
-                cudaFreeAsync(sl->mem, ln.st);
+                if (sl->owns) cudaFreeAsync(sl->mem, ln.st);
                 sl->mem = nullptr;
                 srv->in_use -= sl->bytes;
                 PLAS_CUDA(cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming));
@@ -1313,6 +1383,7 @@ int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int*
         Slot* sl = ln.sl.get();
         if (!sl->cancel) {
             if (sl->job.state_out) to_public(sl->last, sl->job.state_out);
+            if (sl->last.status && !srv->first_error) srv->first_error = status_error(sl->last);
             srv->completed.push_back(sl->job.ticket);
         }
         cudaEventDestroy(ln.done);
@@ -1353,6 +1424,58 @@ int step_concurrent(plas_server* srv, int sweeps, long long* done, int cap, int*
     srv->completed.erase(srv->completed.begin(), srv->completed.begin() + n);
     *n_done = n;
     return PLAS_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// A batch under the box target: every grid on a lane of its own (the box
+// kernels run one grid per launch), in the carved workspaces of the batch.
+int run_lane_batch(int n, const plas_job* jobs, int D, const Weights& w, const plas_schedule& s,
+                   char* base, const std::vector<size_t>& per, cudaStream_t st) {
+    plas_server srv;
+    srv.D = D;
+    srv.w = w;
+    srv.s = s;
+    srv.st = st;
+    srv.policy = PLAS_SERVE_CONCURRENT;
+    if (cudaDeviceGetStreamPriorityRange(&srv.prio_least, &srv.prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        srv.prio_least = srv.prio_greatest = 0;
+    }
+    size_t off = 0;
+    int pending = 0;
+    for (int i = 0; i < n; ++i) {
+        if (per[i] == 0) continue;
+        auto sl = std::make_unique<Slot>();
+        sl->job = job_from(jobs[i]);
+        sl->job.ticket = i;
+        sl->mem = base + off;
+        sl->bytes = per[i];
+        off += per[i];
+        srv.queue.push_back(std::move(sl));
+        ++pending;
+    }
+    std::vector<long long> done((size_t)std::max(n, 1));
+    int rc = PLAS_OK;
+    while (pending > 0) {
+        int got = 0;
+        rc = step_concurrent(&srv, s.iters_per_poll > 0 ? s.iters_per_poll : 8, done.data(), n, &got);
+        if (rc != PLAS_OK) break;
+        pending -= got;
+    }
+    // the lanes' work is ordered before anything later on the caller's stream
+    for (auto& ln : srv.lanes) {
+        cudaStreamSynchronize(ln->st);
+        if (ln->done) cudaEventDestroy(ln->done);
+        ln->eng.reset();
+        cudaStreamDestroy(ln->st);
+        for (cudaStream_t o : ln->old_streams) cudaStreamDestroy(o);
+    }
+    srv.lanes.clear();
+    if (rc == PLAS_OK) rc = srv.first_error;
+    return rc;
 }
 
 }  // namespace

@@ -30,262 +30,18 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "plas_kernels.h"
+#include "sweep_bodies.cuh"
 
 namespace plas {
 
 int num_sms();  // plas_api.cu
 
-static_assert(kFirCols == 128, "four columns per lane");
-
-// Two tilings of the ring kernel (identical results): rows per CTA, ring
-// rows, tap steps per chunk, CTAs per SM.  The large one keeps 16 warps per
-// CTA busy at large radii; the medium one (2 CTAs per SM) overlaps one CTA's
-// first fetch and epilogue with the other's taps at middle radii.  Small
-// radii take fir_direct_kernel below (no ring).
-template <int TY_, int RING_, int CH_, int MINB_>
-struct FirTiling {
-    static constexpr int TY = TY_, RING = RING_, CH = CH_, MINB = MINB_;
-    static constexpr int THREADS = 32 * TY / kFirX;
-    static_assert(RING >= 2 * CH + TY + kFirX, "ring must hold two chunks + span");
-    static_assert(RING % kFirX == 0 && CH % kFirX == 0, "ring and chunk in whole steps of 8");
-    // ring slot of input row t (t >= 0)
-    __device__ static __forceinline__ int slot(int t) {
-        return (RING & (RING - 1)) == 0 ? (t & (RING - 1)) : (t % RING);
-    }
-};
-using FirLarge = FirTiling<128, 256, 56, 1>;
-using FirMedium = FirTiling<64, 128, 24, 2>;
-
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// a / b correctly rounded, from y = RN(1/b): q = RN(a*y) is within one ulp of
-// a/b, the remainder r = a - b*q is exact (one FMA), and RN(q + r*y) is the
-// correctly rounded quotient (Markstein's theorem, IBM J. Res. Dev. 34(1),
-// 1990) as long as nothing underflows or overflows.  Magnitudes outside
-// [2^-60, 2^60] (and zero, NaN, Inf) take the IEEE division itself.
-__device__ __forceinline__ float div_rn(float a, float b, float y) {
-    const float m = fabsf(a);
-    if (!(m >= 0x1p-60f && m <= 0x1p60f)) return __fdiv_rn(a, b);
-    const float q = __fmul_rn(a, y);
-    const float r = __fmaf_rn(-q, b, a);
-    return __fmaf_rn(r, y, q);
-}
-
-// 4-byte copy to shared address sa + OFF (n = 4: copy, n = 0: zero-fill)
-template <int OFF>
-__device__ __forceinline__ void cp_async_f32_at(unsigned sa, const float* gsrc, int n) {
-    asm volatile("cp.async.ca.shared.global [%0+%3], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n),
-                 "n"(OFF)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 template <class TL>
 __global__ void __launch_bounds__(TL::THREADS, TL::MINB) fir_kernel(
     int pass, const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, int D, int gs,
     int ts) {
-    constexpr int X = kFirX;
-    constexpr int kFirTY = TL::TY, kFirChunk = TL::CH;
-    constexpr int kFirThreads = TL::THREADS;
-    constexpr int NW = kFirThreads / 32;
-    const CtaRef cr = resolve_cta(map);
-    const GridRef& gr = grids[cr.g];
-    const DevState* st = gr.st;
-    if (sweep_idle(st)) return;
-    const LevelDesc& lv = gr.lv[st->level];
-
-    const float* in;
-    long long in_row, in_cell;
-    int R, NC, r, rp, ntp;
-    const float* taps;
-    if (pass == 0) {  // along y: G -> H1 ([x][y][d])
-        in = gr.G; in_row = (long long)gr.W * gs; in_cell = gs;
-        R = gr.H; NC = gr.W * D;
-        r = lv.ry; rp = lv.rpy; ntp = lv.ntpy;
-        taps = gr.table + lv.off_ty;
-    } else {          // along x: H1 -> T ([y][x][d], cell stride ts)
-        in = gr.H1; in_row = h1_stride(gr.H, D); in_cell = D;
-        R = gr.W; NC = gr.H * D;
-        r = lv.rx; rp = lv.rpx; ntp = lv.ntpx;
-        taps = gr.table + lv.off_tx;
-    }
-    const int ncol = (NC + kFirCols - 1) / kFirCols;
-    const int c0 = (cr.local % ncol) * kFirCols;
-    const int t0 = (cr.local / ncol) * kFirTY;
-
-    extern __shared__ __align__(16) ulonglong2 ring[];  // kFirRing x 32 lanes x 4 columns
-    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-    // column c = (cell, channel): c / D by multiply-high with ceil(2^32 / D),
-    // exact for c < 2^26 and 2 <= D <= 64 (the host keeps max(H, W) * D <=
-    // 2^26); D = 1 is the identity
-    const unsigned dinv = D > 1 ? (unsigned)((0x100000000ull + (unsigned)D - 1) / (unsigned)D) : 0u;
-    long long inoff[4];
-    int ccell[4], cch[4];
-    bool ok[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = c0 + 32 * k + lane;
-        ok[k] = c < NC;
-        ccell[k] = D > 1 ? (int)__umulhi((unsigned)c, dinv) : c;
-        cch[k] = c - ccell[k] * D;
-        inoff[k] = ok[k] ? (long long)ccell[k] * in_cell + cch[k] : 0;
-    }
-
-    // CTA step range: non-zero taps that reach an in-range row for some output
-    int jlo = max(rp - r, rp - (t0 + kFirTY - 1));
-    jlo = jlo / X * X;
-    const int jhi = min(rp + r, rp + R - 1 - t0);
-    const int jend = min(ntp, (jhi + X) / X * X);
-    // warp step range: the same for this warp's 8 output rows
-    const int rbase = q * X;
-    const int ylo = t0 + rbase;
-    const bool wact = ylo < R;
-    const int yhi = min(ylo + X, R) - 1;
-    int wlo = max(rp - r, rp - yhi);
-    wlo = max(jlo, wlo / X * X);
-    const int whi = min(rp + r, rp + R - 1 - ylo);
-    const int wend = min(jend, (whi + X) / X * X);
-
-    const int span = kFirTY + X;  // rows read past the last step of a chunk
-    // row fetch: ring row t holds input row t0 - rp + t (zero outside [0, R));
-    // per lane the four column pointers, copy sizes and the ring address are
-    // set up once, so a row costs one multiply, four 64-bit adds and four copies
-    const float* colp[4];
-    int csz[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        colp[k] = in + inoff[k];
-        csz[k] = ok[k] ? 4 : 0;
-    }
-    const int tlo = rp - t0, thi = rp - t0 + R;  // ring rows holding grid rows
-    const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring) + 16u * (unsigned)lane;
-    auto fetch = [&](int t) {
-        const unsigned sa = ring_sa + 512u * (unsigned)TL::slot(t);
-        if (t >= tlo && t < thi) {  // warp-uniform
-            const long long off = (long long)(t - tlo) * in_row;
-            cp_async_f32_at<0>(sa, colp[0] + off, csz[0]);
-            cp_async_f32_at<4>(sa, colp[1] + off, csz[1]);
-            cp_async_f32_at<8>(sa, colp[2] + off, csz[2]);
-            cp_async_f32_at<12>(sa, colp[3] + off, csz[3]);
-        } else {
-            cp_async_f32_at<0>(sa, colp[0], 0);
-            cp_async_f32_at<4>(sa, colp[1], 0);
-            cp_async_f32_at<8>(sa, colp[2], 0);
-            cp_async_f32_at<12>(sa, colp[3], 0);
-        }
-    };
-    // taps of a chunk, (k, k) pairs, double-buffered next to the ring
-    __shared__ __align__(16) unsigned long long tapbuf[2][kFirChunk];
-    const unsigned long long* tp = reinterpret_cast<const unsigned long long*>(taps);
-    auto fetch_taps = [&](int from, int to, int b) {  // steps [from, to), multiples of 8
-        for (int p = threadIdx.x; 2 * p < to - from; p += kFirThreads)
-            cp_async_16(&tapbuf[b][2 * p], tp + from + 2 * p);
-    };
-    int loaded_end = min(jlo + kFirChunk, jend) + span;
-    fetch_taps(jlo, min(jlo + kFirChunk, jend), 0);
-    for (int t = jlo + q; t < loaded_end; t += NW) fetch(t);
-    cp_async_wait_all();
-    __syncthreads();
-
-    float2 acc[X][2];
-    float4 win[X];
-#pragma unroll
-    for (int i = 0; i < X; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
-    const float4* fring = reinterpret_cast<const float4*>(ring);
-    bool started = false;
-    int ci = 0;
-    for (int jc = jlo; jc < jend; jc += kFirChunk, ++ci) {
-        const int cend = min(jc + kFirChunk, jend);
-        // the ring holds >= 2 chunks + kFirTY + X rows, so the next chunk's rows
-        // never land on a row that the current chunk still reads; the other tap
-        // buffer was last read by the previous chunk, before its barrier
-        const int next_end = min(cend + kFirChunk, jend) + span;
-        if (cend < jend) fetch_taps(cend, min(cend + kFirChunk, jend), (ci + 1) & 1);
-        for (int t = loaded_end + q; t < next_end; t += NW) fetch(t);
-        loaded_end = max(loaded_end, next_end);
-        const unsigned long long* tb = tapbuf[ci & 1];
-        if (wact) {
-            const int s0 = max(jc, wlo), s1 = min(cend, wend);
-            if (s0 < s1) {
-                if (!started) {
-#pragma unroll
-                    for (int u = 0; u < X; ++u) win[u] = fring[TL::slot(rbase + s0 + u) * 32 + lane];
-                    started = true;
-                }
-                for (int jb = s0; jb < s1; jb += X) {
-                    const int nb = TL::slot(rbase + jb + X);  // a multiple of 8: nb + 7 < RING
-#pragma unroll
-                    for (int u = 0; u < X; u += 2) {
-                        // taps of steps jb+u and jb+u+1 as two (k, k) pairs
-                        const float4 k4 = *reinterpret_cast<const float4*>(tb + (jb - jc + u));
-                        const float2 ka = make_float2(k4.x, k4.y), kb = make_float2(k4.z, k4.w);
-#pragma unroll
-                        for (int i = 0; i < X; ++i) {
-                            const float4 w = win[(u + i) % X];
-                            acc[i][0] = __ffma2_rn(ka, make_float2(w.x, w.y), acc[i][0]);
-                            acc[i][1] = __ffma2_rn(ka, make_float2(w.z, w.w), acc[i][1]);
-                        }
-                        win[u] = fring[(nb + u) * 32 + lane];
-#pragma unroll
-                        for (int i = 0; i < X; ++i) {
-                            const float4 w = win[(u + 1 + i) % X];
-                            acc[i][0] = __ffma2_rn(kb, make_float2(w.x, w.y), acc[i][0]);
-                            acc[i][1] = __ffma2_rn(kb, make_float2(w.z, w.w), acc[i][1]);
-                        }
-                        win[u + 1] = fring[(nb + u + 1) * 32 + lane];
-                    }
-                }
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
-
-    if (wact) {
-        float* out;
-        long long out_row, out_cell;
-        const float* norm;
-        if (pass == 0) {
-            out = gr.H1; out_row = D; out_cell = h1_stride(gr.H, D);
-            norm = gr.table + lv.off_ny;
-        } else {
-            out = gr.T; out_row = ts; out_cell = (long long)gr.W * ts;
-            norm = gr.table + lv.off_nx;
-        }
-        const float* rnorm = norm + ((R + 3) & ~3);  // RN(1/n) per position
-        long long ooff[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ooff[k] = ok[k] ? (long long)ccell[k] * out_cell + cch[k] : 0;
-#pragma unroll
-        for (int i = 0; i < X; ++i) {
-            const int y = ylo + i;
-            if (y < R) {
-                const float nrm = norm[y];
-                const float rcp = rnorm[y];
-                float* orow = out + (long long)y * out_row;
-                const float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (ok[k]) orow[ooff[k]] = div_rn(v[k], nrm, rcp);
-            }
-        }
-    }
-
-    // the iteration's grouping table (the state is not written before the
-    // assignment launch's schedule step)
-    if (pass == 0) write_group_table(gr, lv, st, cr.local, cr.count, kFirThreads);
+    extern __shared__ __align__(16) ulonglong2 ring[];  // TL::RING x 32 lanes x 4 columns
+    fir_ring_body<TL>(pass, grids, resolve_cta(map), D, gs, ts, ring);
 }
 
 // ============================================================================

@@ -41,6 +41,15 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     return cudaMallocAsync(p, bytes, s);
 }
 
+std::atomic<long long> g_persist_zero{0};  // persistent launches still to get a zero wait limit
+
+unsigned long long persist_wait_limit_ns() {
+    long long n = g_persist_zero.load();
+    while (n > 0)
+        if (g_persist_zero.compare_exchange_weak(n, n - 1)) return 0ull;
+    return 2000000000ull;  // two seconds
+}
+
 bool injected_stall() {
     long long n = g_stall_polls.load();
     while (n > 0)
@@ -86,6 +95,7 @@ int validate_schedule(const plas_schedule& s) {
     if (s.trace_cap < 0) return fail(PLAS_ERR_INVALID_ARG, "trace_cap must be >= 0");
     if (!(s.phi0 <= 1e7)) return fail(PLAS_ERR_INVALID_ARG, "phi0 too large");
     if (s.target_mode != 0 && s.target_mode != 1) return fail(PLAS_ERR_INVALID_ARG, "target_mode must be 0 or 1");
+    if (s.persistent < -1 || s.persistent > 1) return fail(PLAS_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
     return PLAS_OK;
 }
 
@@ -184,6 +194,7 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
     w.lv = (LevelDesc*)take(sizeof(LevelDesc) * (size_t)nlev);
     w.table = (float*)take(sizeof(float) * table_floats);
     w.macc = (double*)take(sizeof(double) * 4);
+    w.pctl = (PersistCtl*)take(sizeof(PersistCtl));
     w.sat = sat ? (long long*)take(sizeof(long long) * (size_t)N * ((D + 1) & ~1)) : nullptr;
     if (ws) *ws = w;
     return off;
@@ -293,6 +304,7 @@ int plas_debug_inject(int kind, long long count) {
     if (kind == 0) {
         plas::g_alloc_fail_at.store(0);
         plas::g_stall_polls.store(0);
+        plas::g_persist_zero.store(0);
         return PLAS_OK;
     }
     if (count < 1) return plas::fail(PLAS_ERR_INVALID_ARG, "count must be >= 1");
@@ -302,6 +314,10 @@ int plas_debug_inject(int kind, long long count) {
     }
     if (kind == 2) {
         plas::g_stall_polls.store(count);
+        return PLAS_OK;
+    }
+    if (kind == 3) {
+        plas::g_persist_zero.store(count);
         return PLAS_OK;
     }
     return plas::fail(PLAS_ERR_INVALID_ARG, "unknown injection kind %d", kind);

@@ -21,6 +21,9 @@ int fail(int code, const char* fmt, ...);
 // read-back makes the progress check see no advance.  Neither touches the GPU.
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 bool injected_stall();
+// Wait limit of the persistent sweep's grid barriers: two seconds, or 0 while
+// an injected zero limit is due (plas_debug_inject kind 3).
+unsigned long long persist_wait_limit_ns();
 int check_launch(const char* what);
 int num_sms();
 
@@ -69,6 +72,7 @@ struct Workspace {
     LevelDesc* lv;
     float* table;
     double* macc;
+    PersistCtl* pctl;  // control block of persistent sweeps over this grid
     long long* sat;  // box target: summed-area table, N x round_up(D, 2) int64 (else null)
 };
 size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Workspace* ws,

@@ -147,6 +147,22 @@ void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
                    cudaStream_t s);
 
+// ---- persistent sweep: k iterations of every grid in one cooperative launch ----
+// Work items per phase as the per-class launches would run them (the medium
+// FIR tiling; map == nullptr: one grid, items 0..n-1).  ctl: device control
+// block (reset by the launch).  Waits at the grid barriers give up after
+// limit_ns (PLAS_ERR_TIMEOUT in ctl->status and in every grid's status word).
+// Returns 0, -1 (unsupported D) or -3 (a CUDA call failed).
+struct PersistCtl {
+    unsigned int arrive;  // CTAs arrived at the current barrier
+    unsigned int gen;     // barrier generation
+    int status;           // 0, or PLAS_ERR_TIMEOUT after a wait gave up
+    int pad_;
+};
+int launch_persist(const GridRef* grids, int ngrids, const CtaMap* map_y, int n_y,
+                   const CtaMap* map_x, int n_x, const CtaMap* map_a, int n_a, int D, int k,
+                   double tol, PersistCtl* ctl, unsigned long long limit_ns, cudaStream_t s);
+
 // ---- box target (target_mode 1): one grid -------------------------------------
 // (prepare_box_launches: the shared-memory opt-in, once per device, before a
 // stream capture; launch_box_target calls it too)

@@ -82,7 +82,49 @@ def test_box_snapshot_parity(plas, orc, side, radii):
         assert int(full.trace_S[start].item()) == int(want["trace_S"][0])
 
 
-def test_box_mode_rejected_for_batches(plas):
-    x = torch.rand(32 * 32, 3, device="cuda")
+BOX_GRIDS = [(40, 40, 3), (17, 64, 3), (64, 17, 3), (48, 80, 3)]
+
+
+def test_box_mode_batch_matches_oracle(plas, orc):
+    """Box-target batches run one lane (stream + engine) per grid; every
+    grid's permutation and final state equal the oracle's box-mode sort."""
+    jobs, wants = [], []
+    for i, (H, W, D) in enumerate(BOX_GRIDS):
+        x = np.random.default_rng(70 + i).random((H * W, D), dtype=np.float32)
+        jobs.append({"x": _cuda(x), "H": H, "W": W, "seed": 7 + i})
+        wants.append(orc.sort(x, H, W, seed=7 + i, sched=orc.default_schedule(target_mode=1)))
+    res = plas.batch_sort(jobs, schedule=plas.Schedule(target_mode=1))
+    for r, want in zip(res, wants):
+        assert np.array_equal(r.perm.cpu().numpy(), want["perm"])
+        assert r.state["it"] == want["iterations"]
+        assert r.state["d_last"] == want["state"].d_last
+
+
+def test_box_mode_server_matches_alone(plas):
+    """A box-target server takes the concurrent policy (any other is
+    refused); requests arriving while others run give their results alone."""
+    sched = plas.Schedule(target_mode=1)
+    with pytest.raises(ValueError):
+        plas.Server(3, schedule=sched, policy="bogus")
     with pytest.raises(RuntimeError):
-        plas.batch_sort([{"x": x, "H": 32, "W": 32}], schedule=plas.Schedule(target_mode=1))
+        plas.Server(3, schedule=sched, policy="all")
+    srv = plas.Server(3, schedule=sched)
+    reqs, tickets, results = [], {}, {}
+    for i, (H, W, D) in enumerate(BOX_GRIDS):
+        x = torch.from_numpy(np.random.default_rng(90 + i).random((H * W, D), dtype=np.float32)).cuda()
+        reqs.append((x, H, W, 3 + i))
+    tickets[srv.submit(reqs[0][0], reqs[0][1], reqs[0][2], seed=reqs[0][3])] = reqs[0]
+    steps = 0
+    late = reqs[1:]
+    while len(results) < len(reqs):
+        results.update(srv.step(sweeps=4))
+        steps += 1
+        if late and steps % 2 == 0:
+            r = late.pop(0)
+            tickets[srv.submit(r[0], r[1], r[2], seed=r[3])] = r
+        assert steps < 100000
+    srv.close()
+    for t, (x, H, W, seed) in tickets.items():
+        one = plas.sort(x, H, W, seed=seed, schedule=sched)
+        assert torch.equal(results[t].perm, one.perm)
+        assert results[t].state["it"] == one.state["it"]

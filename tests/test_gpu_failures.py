@@ -125,3 +125,25 @@ def test_injection_arguments(plas):
     assert lib.plas_debug_inject(1, 0) == -1
     assert lib.plas_debug_inject(9, 1) == -1
     assert lib.plas_debug_inject(0, 0) == 0
+
+
+def test_persistent_sweep_barrier_timeout(plas):
+    """A zero wait limit at the persistent sweep's grid barriers (injected on
+    the host): the first wait gives up, the launch ends and the call returns
+    PLAS_ERR_TIMEOUT; the GPU stays usable and the next batch is correct."""
+    lib = plas.load()
+    jobs = []
+    for i, (H, W) in enumerate([(40, 40), (33, 48), (64, 20)]):
+        x, c = synth.gaussians_3dgs(H * W, seed=20 + i)
+        jobs.append({"x": torch.from_numpy(x).cuda(), "H": H, "W": W,
+                     "carried": torch.from_numpy(c).cuda(), "seed": i})
+    sched = plas.Schedule(persistent=1)
+    assert lib.plas_debug_inject(3, 1) == 0
+    with pytest.raises(RuntimeError) as e:
+        plas.batch_sort(jobs, schedule=sched)
+    assert _status(e.value) == -4
+    lib.plas_debug_inject(0, 0)
+    res = plas.batch_sort(jobs, schedule=sched)
+    for j, r in zip(jobs, res):
+        one = plas.sort(j["x"], j["H"], j["W"], carried=j["carried"], seed=j["seed"])
+        assert torch.equal(r.perm, one.perm) and torch.equal(r.carried, one.carried)

@@ -112,13 +112,18 @@ def test_full_sort_matches_oracle_fixture(plas, name, side):
     assert abs(r.state["d_last"] - fx["mean_l2_to_target"]) <= 1e-4 * fx["mean_l2_to_target"]
 
 
-def test_batch_sort_matches_oracle(plas, cases):
+@pytest.mark.parametrize("persistent", [-1, 1])
+def test_batch_sort_matches_oracle(plas, cases, persistent):
+    """Separate launches per kernel class (graph-replayed) and the persistent
+    cooperative sweep (all grids, k iterations per launch, grid-wide
+    barriers) give every grid the oracle's result."""
     reqs = [_gpu(c) for c in cases]
-    for res, case in zip(plas.batch_sort(reqs), cases):
+    sched = plas.Schedule(persistent=persistent)
+    for res, case in zip(plas.batch_sort(reqs, schedule=sched), cases):
         _check(res, case)
 
 
-@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent"])
+@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent", "adaptive"])
 def test_server_matches_oracle(plas, cases, policy):
     """Three requests first, the others (the 512 x 512 one last) arriving
     while those run; every result equals the oracle's."""

@@ -175,21 +175,27 @@ def test_poll_batch_size_does_not_change_result(plas):
 
 
 def test_launch_modes_give_identical_results(plas, orc):
-    """Graph replay, direct launches and event-profiled launches run the same
-    kernels with the same arguments: the permutation and the schedule trace
-    match each other and the oracle."""
+    """Graph replay, direct launches, event-profiled launches and the
+    persistent cooperative sweep run the same kernel bodies on the same work
+    items: the permutation and the schedule trace match each other and the
+    oracle."""
     side = 48
     x = synth.rgb_uniform(side, seed=6)
     xc = _cuda(x)
-    g = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14)
+    g = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
+                  schedule=plas.Schedule(persistent=-1))
     d = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
-                  schedule=plas.Schedule(graphs=False))
+                  schedule=plas.Schedule(graphs=False, persistent=-1))
     p = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
                   schedule=plas.Schedule(profile=True, iters_per_poll=3))
+    c = plas.sort(xc, side, side, seed=6, want_stats=True, trace_cap=1 << 14,
+                  schedule=plas.Schedule(persistent=1, iters_per_poll=5))
     assert g.stats["graph_launches"] > 0 and g.stats["graph_captures"] >= 1
     assert d.stats["graph_launches"] == 0 and p.stats["graph_launches"] == 0
+    # one cooperative launch per batch of five sweeps
+    assert c.stats["graph_launches"] == 0 and c.stats["launches"] < c.state["it"]
     want = orc.sort(x, side, side, seed=6)
-    for r in (g, d, p):
+    for r in (g, d, p, c):
         assert np.array_equal(r.perm.cpu().numpy(), want["perm"])
         n = r.state["it"]
         assert r.trace_S[:n].cpu().numpy().tolist() == want["trace_S"][:n].tolist()

@@ -53,7 +53,7 @@ def test_batch_sort_d3(plas):
         assert torch.equal(got.perm, one.perm) and got.state["it"] == one.state["it"]
 
 
-@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent"])
+@pytest.mark.parametrize("policy", ["fifo_fill", "shortest_first", "all", "concurrent", "adaptive"])
 def test_server_arrivals_while_running(plas, policy):
     reqs = _requests(seed0=10)
     srv = plas.Server(14, policy=policy)
