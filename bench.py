@@ -661,6 +661,61 @@ def run_loss(args):
     print(json.dumps(line), flush=True)
 
 
+def run_loss_loop(args):
+    """The smoothness loss inside training (Sec. 3.2 with the sort of Sec. 3.1
+    between steps) on the 1024 x 1024 x 59 grid: Adam (lr 1e-3) on the
+    squared smoothness loss (sigma 1, 7 x 7) for --loop-steps steps; every 100
+    steps the grid is re-sorted on its 14 sort channels (warm start from the
+    current arrangement), and all 59 channels and both Adam moments follow
+    the permutation.  Reported: ms per optimizer step (loss forward +
+    hand-written backward + Adam update, CUDA events on the launching stream,
+    re-sorts excluded), ms per re-sort and the loss before and after.  The
+    loss and gradient against FP64 at every re-sort are checked by
+    tests/test_gpu_loss.py::test_loss_loop_full_size_with_resorts."""
+    import torch
+    import paper_2312_13299_gb300 as plas
+    from paper_2312_13299_gb300 import synth
+    plas.load()
+    H = W = 1024
+    P = torch.from_numpy(synth.loss_grid(H, W, seed=0).reshape(H * W, -1).astype("float32")).cuda()
+    P.requires_grad_(True)
+    opt = torch.optim.Adam([P], lr=1e-3)
+    stream = torch.cuda.current_stream()
+    step_ms, sort_ms, losses = 0.0, [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for step in range(args.loop_steps):
+        if step % 100 == 0:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.no_grad():
+                r = plas.sort(P[:, :14].contiguous(), H, W, seed=step,
+                              schedule=plas.Schedule(shuffle_init=(step == 0)))
+                P.copy_(plas.gather_rows(P.detach(), r.perm))
+                for v in (opt.state[P].values() if P in opt.state else []):
+                    if torch.is_tensor(v) and v.dim() == 2:
+                        v.copy_(plas.gather_rows(v, r.perm))
+            torch.cuda.synchronize()
+            sort_ms.append((time.perf_counter() - t0) * 1e3)
+        e0.record(stream)
+        opt.zero_grad(set_to_none=False)
+        loss = plas.smooth_loss(P.reshape(H, W, -1), 1.0, 7)
+        loss.backward()
+        opt.step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms += e0.elapsed_time(e1)
+        if step == 0 or step == args.loop_steps - 1:
+            losses.append(float(loss.item()))
+    line = {"metric": "smoothness-loss training loop with re-sorts, 1024x1024x59",
+            "value": round(step_ms / args.loop_steps, 4), "unit": "ms per optimizer step",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic (3DGS-shaped 14 + 45 channels)",
+            "config": {"steps": args.loop_steps, "resort_every": 100, "optimizer": "Adam lr 1e-3",
+                       "loss": "squared, sigma 1, 7x7, unit weights"},
+            "resort_ms": [round(v, 1) for v in sort_ms], "loss_first": losses[0], "loss_last": losses[-1]}
+    print(json.dumps(line), flush=True)
+
+
 def run_threshold_sweep(args):
     """Sorting quality against runtime over the stall threshold (the
     break-threshold study of the supplementary), for the Gaussian and the box
@@ -809,6 +864,10 @@ def main():
                     "(0 = the schedule's default), to profile small radii directly")
     ap.add_argument("--serve", action="store_true",
                     help="served-stream benchmark (continuous batching vs plain), own JSON line")
+    ap.add_argument("--loss-loop", action="store_true",
+                    help="smoothness loss inside an Adam loop with a re-sort every 100 steps "
+                         "(1024x1024x59), own JSON line")
+    ap.add_argument("--loop-steps", type=int, default=1000)
     ap.add_argument("--loss", action="store_true",
                     help="smoothness-loss fwd/bwd benchmark on 1024x1024x59, own JSON line")
     ap.add_argument("--threshold-sweep", action="store_true",
@@ -837,6 +896,9 @@ def main():
         return
     if args.loss:
         run_loss(args)
+        return
+    if args.loss_loop:
+        run_loss_loop(args)
         return
     if args.threshold_sweep:
         run_threshold_sweep(args)

@@ -58,7 +58,8 @@ class Schedule(ctypes.Structure):
                 ("phi_min", ctypes.c_double), ("tol", ctypes.c_double),
                 ("sigma_ratio", ctypes.c_double), ("min_block", ctypes.c_int),
                 ("shuffle_init", ctypes.c_int), ("normalize", ctypes.c_int),
-                ("target_mode", ctypes.c_int), ("max_iters", ctypes.c_longlong)]
+                ("target_mode", ctypes.c_int), ("max_iters", ctypes.c_longlong),
+                ("edge_blocks", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -77,7 +78,8 @@ def default_schedule(**kw) -> Schedule:
     """Defaults: phi0 = w/2-1, shrink 0.95, stop below 1 (Sec. 3.1); tol 1e-4
     (supplementary); min block 16 (Sec. 3.1); sigma = 2 phi (paper silent)."""
     s = Schedule(phi0=0.0, shrink=0.95, phi_min=1.0, tol=1e-4, sigma_ratio=2.0,
-                 min_block=16, shuffle_init=1, normalize=1, target_mode=0, max_iters=0)
+                 min_block=16, shuffle_init=1, normalize=1, target_mode=0, max_iters=0,
+                 edge_blocks=0)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -156,6 +156,12 @@ typedef struct {
     int normalize;      /* 1: per-channel [0,1] normalisation (Sec. 3.1)      */
     int target_mode;    /* 0: Gaussian target (Sec. 3.1); 1: box target      */
     long long max_iters;/* stop after this many iterations in total; 0 = none */
+    int edge_blocks;    /* reading of the borders after the shift (Sec. 3.1): */
+                        /* 0 (default) only whole blocks are re-assigned; 1  */
+                        /* the blocks cut by the grid border are too, each   */
+                        /* group of four whose cells all lie inside the grid */
+                        /* (the others stay put)                             */
+    int pad_;
 } orc_schedule;
 
 typedef struct {
@@ -470,10 +476,17 @@ long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t
         else
             orc_blur(G, gs, H, W, D, r, sigma, T);
 
-        /* (2) blocks shifted by a random (dy, dx) */
+        /* (2) blocks shifted by a random (dy, dx): the whole blocks from
+         *     (dy, dx) on, or (edge_blocks) every block that meets the grid */
         int dy, dx;
         orc_shift(seed, (uint64_t)s.epoch, beta, H, W, &dy, &dx);
-        const int nby = (H - dy) / beta, nbx = (W - dx) / beta;
+        int nby = (H - dy) / beta, nbx = (W - dx) / beta;
+        if (sch->edge_blocks) {
+            if (dy > 0) dy -= beta;
+            if (dx > 0) dx -= beta;
+            nby = (H - dy + beta - 1) / beta;
+            nbx = (W - dx + beta - 1) / beta;
+        }
 
         /* (3) one random permutation of a block's cells, shared by all blocks */
         const uint32_t nb2 = (uint32_t)beta * (uint32_t)beta;
@@ -489,10 +502,14 @@ long long orc_sort(const float* x, int H, int W, int D, const float* w, uint64_t
             const long blk = bg / ngroups, g = bg % ngroups;
             const int oy = dy + (int)(blk / nbx) * beta, ox = dx + (int)(blk % nbx) * beta;
             long pos[4];
+            int inside = 1;
             for (int k = 0; k < 4; ++k) {
                 uint32_t l = pi[4 * g + k];
-                pos[k] = (long)(oy + (int)(l / (uint32_t)beta)) * W + (ox + (int)(l % (uint32_t)beta));
+                const int y = oy + (int)(l / (uint32_t)beta), x = ox + (int)(l % (uint32_t)beta);
+                inside = inside && y >= 0 && y < H && x >= 0 && x < W;
+                pos[k] = (long)y * W + x;
             }
+            if (!inside) continue; /* only with edge_blocks: a cell beyond the border */
             float C[16];
             for (int i = 0; i < 4; ++i)
                 for (int j = 0; j < 4; ++j)
