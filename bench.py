@@ -55,7 +55,7 @@ FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
 # keyed by the sha1 of the kernel source it was taken on: a stale hash
 # reports null.
 NCU_TRAFFIC = {
-    ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 84955336, "src": "793aa4f395a0"},
+    ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 84966598, "src": "90dec4ec9721"},
 }
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
@@ -450,9 +450,11 @@ def run_plas(args):
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"value": None, "error": repr(e)}
     if args.serve_in_bench and world == 1:
+        # the server's latency policy (fifo_fill) under Poisson arrivals and
+        # its throughput policy (all) under a burst, each against plain
         try:
-            line["serve"] = serve_compare(args.requests, ["poisson", "burst"],
-                                          [p for p in args.serve_policy.split(",") if p], args.sweeps)
+            pairs = [(pp.split(":")[0], [pp.split(":")[1]]) for pp in args.serve_pairs.split(",") if pp]
+            line["serve"] = serve_compare(args.requests, [], [], args.sweeps, pairs=pairs)
         except Exception as e:  # reported, never silently replaced
             line["serve"] = {"error": repr(e)}
     print(json.dumps(line), flush=True)
@@ -501,7 +503,7 @@ def run_reference(args):
         pg.destroy_process_group()
 
 
-def serve_compare(n, patterns, policies, sweeps, budget_bytes=40 * 10 ** 9):
+def serve_compare(n, patterns, policies, sweeps, budget_bytes=40 * 10 ** 9, pairs=None):
     """Served stream against the plain path on one GPU: n requests (sides
     U{128..1024}, 14 sort + 45 carried channels, seeded) under an admission
     budget, through the server (continuous batching, one run per policy) and
@@ -586,10 +588,12 @@ def serve_compare(n, patterns, policies, sweeps, budget_bytes=40 * 10 ** 9):
     pats = {"poisson": [a for a, _ in base], "overload": [a * 0.8 / 1.25 for a, _ in base],
             "burst": [0.0] * n}
     out = {}
-    for pat in patterns:
+    # (pattern, policies) to run; pairs overrides the full cross product
+    plan = pairs if pairs else [(pat, policies) for pat in patterns]
+    for pat, pols in plan:
         arr = pats[pat]
         out[pat] = {"plain": summary(*plain(arr))}
-        for pol in policies:
+        for pol in pols:
             out[pat]["served_" + pol] = summary(*served(arr, pol))
     return {"workload": f"{n} requests, sides U{{128..1024}}, 14 sort + 45 carried fp32, "
                         f"{budget_bytes / 1e9:.0f} GB admission budget, seed 0",
@@ -885,8 +889,8 @@ def main():
                     "(poisson = 0.8 x plain capacity, overload = 1.25 x, burst)")
     ap.add_argument("--no-serve", dest="serve_in_bench", action="store_false",
                     help="leave the served-stream comparison out of the default line")
-    ap.add_argument("--serve-policy", default="adaptive",
-                    help="server policies of the default line's served-stream comparison")
+    ap.add_argument("--serve-pairs", default="poisson:fifo_fill,burst:all",
+                    help="PATTERN:POLICY pairs of the default line's served-stream comparison")
     args = ap.parse_args()
     if args.ncu_case > 0:
         run_ncu_case(args)
