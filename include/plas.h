@@ -97,6 +97,12 @@ typedef struct plas_schedule {
                         /* a barrier that waits 2 s gives up with            */
                         /* PLAS_ERR_TIMEOUT (the GPU stays usable).  The     */
                         /* concurrent server policy never uses it.           */
+    int checked;        /* 1: checked run (plas_sort): 256-byte guard bands   */
+                        /* between the workspace regions are filled with a   */
+                        /* pattern and verified after the sort, and the      */
+                        /* assignment checks every grouping-table entry and  */
+                        /* cell position against the grid; a violation      */
+                        /* returns PLAS_ERR_INTERNAL.  0 (default): off      */
     long long* trace_S; /* device or NULL: trace_S[it] = fixed-point residual */
                         /* sum of iteration it (mean L2 distance * N * 2^k)  */
     int* trace_level;   /* device or NULL: level of iteration it             */
@@ -618,7 +624,10 @@ const char* plas_last_error(void);  /* thread-local; "" if none */
  *   kind 3: the next count persistent sweep launches (plas_schedule.
  *           persistent) get a zero wait limit at their grid-wide barriers:
  *           the first wait gives up at once, the launch ends early and the
- *           call returns PLAS_ERR_TIMEOUT (the GPU stays usable).
+ *           call returns PLAS_ERR_TIMEOUT (the GPU stays usable);
+ *   kind 4: the next count checked sorts (plas_schedule.checked) get one
+ *           byte of their first guard band overwritten by the host after
+ *           the bands are filled: the sort returns PLAS_ERR_INTERNAL.
  * Process-wide (all threads).  Returns PLAS_OK or PLAS_ERR_INVALID_ARG
  * (unknown kind, count < 1).
  */

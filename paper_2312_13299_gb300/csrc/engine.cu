@@ -176,6 +176,12 @@ class Engine {
         ref.trace_S = j.trace_S; ref.trace_level = j.trace_level; ref.trace_cap = j.trace_cap;
         ref.target_mode = s_.target_mode;
         ref.sat = sl->ws.sat;
+        ref.checked = s_.checked;
+        if (s_.checked) {
+            launch_fill_guards(sl->ws.guards, st_);
+            if (injected_guard_damage() && sl->ws.guards.n > 0)  // a planted overwrite (tests)
+                PLAS_CUDA(cudaMemsetAsync(sl->ws.guards.at[0] + 17, 0, 1, st_));
+        }
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st_));
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.ref, &ref, sizeof(GridRef), cudaMemcpyHostToDevice, st_));
         PLAS_CUDA(cudaMemcpyAsync(sl->ws.lv, sl->geo.lv.data(), sizeof(LevelDesc) * sl->nlev,
@@ -427,7 +433,7 @@ class Engine {
                         if (s_.target_mode != 1)
                             launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
                         break;
-                    default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st); break;
+                    default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st, s_.checked != 0); break;
                 }
                 if (events) end(e0, c);
             }
@@ -511,6 +517,7 @@ class Engine {
             r.trace_cap = sl->job.trace_cap;
             r.target_mode = s_.target_mode;
             r.sat = sl->ws.sat;
+            r.checked = s_.checked;
         }
         // the persistent sweep runs the medium FIR tiling, separate launches
         // the large one
@@ -598,11 +605,25 @@ class Engine {
     long long persist_launches_ = 0;
 };
 
+// Checked runs: every guard band must still hold its pattern.
+int verify_guards(const Workspace& ws, cudaStream_t st) {
+    unsigned int* bad = reinterpret_cast<unsigned int*>(ws.macc);  // scratch, before the metrics
+    unsigned int h = 0;
+    PLAS_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
+    launch_check_guards(ws.guards, bad, st);
+    PLAS_CUDA(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PLAS_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(PLAS_ERR_INTERNAL, "checked run: %u guard bytes between workspace regions were overwritten", h);
+    return PLAS_OK;
+}
+
 int status_error(const DevState& st) {
     if (st.nonfinite) return fail(PLAS_ERR_NONFINITE, "sort input holds NaN or Inf");
     if (st.bad_index) return fail(PLAS_ERR_INVALID_ARG, "perm_init holds an index outside [0, N)");
     if (st.status == PLAS_ERR_TIMEOUT)
         return fail(PLAS_ERR_TIMEOUT, "a bounded device wait gave up (no progress for 2 s)");
+    if (st.status == PLAS_ERR_INTERNAL)
+        return fail(PLAS_ERR_INTERNAL, "checked run: a grouping entry or cell position outside the grid");
     return fail(PLAS_ERR_INTERNAL, "device status %d", st.status);
 }
 
@@ -751,6 +772,7 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
         Engine eng(D, w, s, st);
         rc = eng.admit(&sl);
         if (rc == PLAS_OK) rc = run_all(eng, s);
+        if (rc == PLAS_OK && s.checked) rc = verify_guards(sl.ws, st);
         if (rc == PLAS_OK && stats) {
             memset(stats, 0, sizeof(*stats));
             double macc[4] = {0, 0, 0, 0};

@@ -50,6 +50,15 @@ unsigned long long persist_wait_limit_ns() {
     return 2000000000ull;  // two seconds
 }
 
+std::atomic<long long> g_guard_damage{0};  // checked runs still to get a damaged guard band
+
+bool injected_guard_damage() {
+    long long n = g_guard_damage.load();
+    while (n > 0)
+        if (g_guard_damage.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 bool injected_stall() {
     long long n = g_stall_polls.load();
     while (n > 0)
@@ -179,12 +188,16 @@ size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Work
                         char* base, bool sat) {
     const long long N = (long long)H * W;
     size_t off = 0;
+    Workspace w{};
+    // every region is followed by a guard band (filled and verified by
+    // checked runs; otherwise unused)
     auto take = [&](size_t bytes) {
         size_t o = off;
         off = align_up(off + bytes, 256);
+        if (w.guards.n < kMaxGuards) w.guards.at[w.guards.n++] = base ? (unsigned char*)(base + off) : nullptr;
+        off += kGuardBytes;
         return base ? (void*)(base + o) : nullptr;
     };
-    Workspace w{};
     w.st = (DevState*)take(sizeof(DevState));
     w.ref = (GridRef*)take(sizeof(GridRef));
     w.G = (float*)take(sizeof(float) * (size_t)N * grid_stride(D));
@@ -305,6 +318,7 @@ int plas_debug_inject(int kind, long long count) {
         plas::g_alloc_fail_at.store(0);
         plas::g_stall_polls.store(0);
         plas::g_persist_zero.store(0);
+        plas::g_guard_damage.store(0);
         return PLAS_OK;
     }
     if (count < 1) return plas::fail(PLAS_ERR_INVALID_ARG, "count must be >= 1");
@@ -318,6 +332,10 @@ int plas_debug_inject(int kind, long long count) {
     }
     if (kind == 3) {
         plas::g_persist_zero.store(count);
+        return PLAS_OK;
+    }
+    if (kind == 4) {
+        plas::g_guard_damage.store(count);
         return PLAS_OK;
     }
     return plas::fail(PLAS_ERR_INVALID_ARG, "unknown injection kind %d", kind);

@@ -24,6 +24,9 @@ bool injected_stall();
 // Wait limit of the persistent sweep's grid barriers: two seconds, or 0 while
 // an injected zero limit is due (plas_debug_inject kind 3).
 unsigned long long persist_wait_limit_ns();
+// A planted overwrite of a checked run's first guard band is due
+// (plas_debug_inject kind 4).
+bool injected_guard_damage();
 int check_launch(const char* what);
 int num_sms();
 
@@ -74,6 +77,7 @@ struct Workspace {
     double* macc;
     PersistCtl* pctl;  // control block of persistent sweeps over this grid
     long long* sat;  // box target: summed-area table, N x round_up(D, 2) int64 (else null)
+    Guards guards;   // the guard band after each region (checked runs fill them)
 };
 size_t workspace_layout(int H, int W, int D, int nlev, size_t table_floats, Workspace* ws,
                         char* base, bool sat = false);

@@ -76,6 +76,7 @@ struct GridRef {
     int* trace_level;     // optional per-iteration level
     long long trace_cap;
     long long* sat;       // box target: N x round_up(D, 2) int64 summed-area table
+    int checked;          // checked run: device bounds checks into the status word
 };
 
 // CTA -> grid map entry of a batched launch.
@@ -145,7 +146,7 @@ void prepare_fir_launches();
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s, const FirTma* tma = nullptr);
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
-                   cudaStream_t s);
+                   cudaStream_t s, bool checked = false);
 
 // ---- persistent sweep: k iterations of every grid in one cooperative launch ----
 // Work items per phase as the per-class launches would run them (the medium
@@ -184,6 +185,18 @@ void launch_copy_features(const float* T, int N, int D, int ts, float* out, cuda
 // acc[0] sum of neighbour L2, acc[1] sum |diff|*scale, acc[2] sum (|diff|*scale)^2
 void launch_neighbour_metrics(const float* g, int stride, int H, int W, int D, double scale,
                               double* acc, int num_sms, cudaStream_t s);
+
+// ---- checked runs ---------------------------------------------------------------
+constexpr int kGuardBytes = 256;          // guard band after every workspace region
+constexpr unsigned char kGuardByte = 0xA5;
+constexpr int kMaxGuards = 16;
+struct Guards {
+    unsigned char* at[kMaxGuards];
+    int n;
+};
+// bad[0] = number of guard bytes that differ from kGuardByte
+void launch_fill_guards(const Guards& g, cudaStream_t s);
+void launch_check_guards(const Guards& g, unsigned int* bad, cudaStream_t s);
 
 // ---- errors (thread-local message behind plas_last_error) ---------------------
 void set_last_error(const char* msg);

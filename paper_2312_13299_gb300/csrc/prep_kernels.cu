@@ -402,4 +402,24 @@ void launch_neighbour_metrics(const float* g, int stride, int H, int W, int D, d
     neighbour_metrics_kernel<<<blocks, 256, 0, s>>>(g, stride, H, W, D, scale, acc);
 }
 
+// ---- checked runs: guard bands between workspace regions ---------------------
+__global__ void fill_guards_kernel(Guards g) {
+    for (int k = blockIdx.x; k < g.n; k += gridDim.x)
+        for (int b = threadIdx.x; b < kGuardBytes; b += blockDim.x) g.at[k][b] = kGuardByte;
+}
+
+__global__ void check_guards_kernel(Guards g, unsigned int* bad) {
+    for (int k = blockIdx.x; k < g.n; k += gridDim.x)
+        for (int b = threadIdx.x; b < kGuardBytes; b += blockDim.x)
+            if (g.at[k][b] != kGuardByte) atomicAdd(bad, 1u);
+}
+
+void launch_fill_guards(const Guards& g, cudaStream_t s) {
+    if (g.n > 0) fill_guards_kernel<<<g.n, 256, 0, s>>>(g);
+}
+
+void launch_check_guards(const Guards& g, unsigned int* bad, cudaStream_t s) {
+    if (g.n > 0) check_guards_kernel<<<g.n, 256, 0, s>>>(g, bad);
+}
+
 }  // namespace plas

@@ -31,10 +31,10 @@ namespace plas {
 // target after the swap is added to an exact fixed-point sum; the last CTA of
 // the grid to finish runs the schedule step (Sec. 3.1).
 // ============================================================================
-template <int D>
+template <int D, bool CHECKED>
 __global__ void __launch_bounds__(kAssignThreads, 4) assign_kernel(
     const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, double tol) {
-    assign_body<D, true>(grids, resolve_cta(map), tol);
+    assign_body<D, true, CHECKED>(grids, resolve_cta(map), tol);
 }
 
 int assign_ctas(int H, int W, int num_sms, int per_sm) {
@@ -47,16 +47,19 @@ int assign_ctas(int H, int W, int num_sms, int per_sm) {
 
 template <int D>
 static void launch_assign_t(const GridRef* grids, const CtaMap* map, int ctas, double tol,
-                            cudaStream_t s) {
-    assign_kernel<D><<<ctas, kAssignThreads, 0, s>>>(grids, map, tol);
+                            bool checked, cudaStream_t s) {
+    if (checked)
+        assign_kernel<D, true><<<ctas, kAssignThreads, 0, s>>>(grids, map, tol);
+    else
+        assign_kernel<D, false><<<ctas, kAssignThreads, 0, s>>>(grids, map, tol);
 }
 
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool checked) {
     if (ctas <= 0) return;
     switch (D) {
 #define PLAS_CASE(d) \
-    case d: launch_assign_t<d>(grids, map, ctas, tol, s); break;
+    case d: launch_assign_t<d>(grids, map, ctas, tol, checked, s); break;
         PLAS_CASE(1) PLAS_CASE(2) PLAS_CASE(3) PLAS_CASE(4) PLAS_CASE(5) PLAS_CASE(6)
         PLAS_CASE(7) PLAS_CASE(8) PLAS_CASE(9) PLAS_CASE(10) PLAS_CASE(11) PLAS_CASE(12)
         PLAS_CASE(13) PLAS_CASE(14) PLAS_CASE(15) PLAS_CASE(16) PLAS_CASE(20) PLAS_CASE(24)

@@ -383,8 +383,9 @@ __device__ __forceinline__ T ldg_ro(const T* p) {
 // One work item of the assignment with the whole CTA (kAssignThreads
 // threads): slice cr.local of cr.count of grid cr.g's groups and cells.  RO:
 // the target and the grouping table are read through the read-only path
-// (they are not written during the launch).
-template <int D, bool RO>
+// (they are not written during the launch).  CHECKED: every grouping entry
+// and cell position is checked against the block and the grid first.
+template <int D, bool RO, bool CHECKED = false>
 __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, const CtaRef cr,
                                             double tol) {
     constexpr int GS = (D + 1 + 3) & ~3, TS = (D + 3) & ~3;
@@ -439,6 +440,19 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
             const int ly = (int)(ls[k] / (uint32_t)beta);
             const int lx = (int)(ls[k] - (uint32_t)ly * (uint32_t)beta);
             pos[k] = (oy + ly) * W + (ox + lx);
+        }
+        if (CHECKED) {
+            // checked run: every grouping entry must lie in the block and every
+            // cell in the grid; a violation is recorded and the warp's groups skipped
+            bool inb = true;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                inb = inb && ls[k] < (uint32_t)(beta * beta) && pos[k] >= 0 && pos[k] < H * W &&
+                      oy + (int)(ls[k] / (uint32_t)beta) < H && ox + (int)(ls[k] % (uint32_t)beta) < W;
+            if (!__all_sync(0xFFFFFFFFu, !active || inb)) {
+                if (active && !inb) atomicCAS(&st->status, 0, -7);  // PLAS_ERR_INTERNAL
+                continue;
+            }
         }
         float grow[GS];
         load_row4_rw<GS / 4>(G + (size_t)pick4i(pos, qi) * GS, grow);

@@ -147,3 +147,25 @@ def test_persistent_sweep_barrier_timeout(plas):
     for j, r in zip(jobs, res):
         one = plas.sort(j["x"], j["H"], j["W"], carried=j["carried"], seed=j["seed"])
         assert torch.equal(r.perm, one.perm) and torch.equal(r.carried, one.carried)
+
+
+def test_checked_run_matches_oracle_and_detects_a_planted_overwrite(plas, orc):
+    """schedule.checked: guard bands between the workspace regions are filled
+    and verified after the sort, and the assignment checks every grouping
+    entry and cell position.  A healthy run passes and equals the oracle; a
+    guard byte overwritten by the host after the fill (injected) is reported
+    as PLAS_ERR_INTERNAL; the next checked run passes again."""
+    lib = plas.load()
+    x, c = synth.gaussians_3dgs(48 * 48, seed=8)
+    xc, cc = torch.from_numpy(x).cuda(), torch.from_numpy(c).cuda()
+    sched = plas.Schedule(checked=True)
+    got = plas.sort(xc, 48, 48, carried=cc, seed=8, schedule=sched)
+    want = orc.sort(x, 48, 48, seed=8)
+    assert np.array_equal(got.perm.cpu().numpy(), want["perm"])
+    assert lib.plas_debug_inject(4, 1) == 0
+    with pytest.raises(RuntimeError) as e:
+        plas.sort(xc, 48, 48, carried=cc, seed=8, schedule=sched)
+    assert _status(e.value) == PLAS_ERR_INTERNAL and "guard" in str(e.value)
+    lib.plas_debug_inject(0, 0)
+    again = plas.sort(xc, 48, 48, carried=cc, seed=8, schedule=sched)
+    assert torch.equal(again.perm, got.perm)
