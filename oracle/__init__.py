@@ -76,10 +76,12 @@ class State(ctypes.Structure):
 
 def default_schedule(**kw) -> Schedule:
     """Defaults: phi0 = w/2-1, shrink 0.95, stop below 1 (Sec. 3.1); tol 1e-4
-    (supplementary); min block 16 (Sec. 3.1); sigma = 2 phi (paper silent)."""
+    (supplementary); min block 16 (Sec. 3.1); sigma = 2 phi (paper silent);
+    the blocks cut by the grid border take part (Sec. 3.1: the shifted
+    blocks cover the whole grid, borders included)."""
     s = Schedule(phi0=0.0, shrink=0.95, phi_min=1.0, tol=1e-4, sigma_ratio=2.0,
                  min_block=16, shuffle_init=1, normalize=1, target_mode=0, max_iters=0,
-                 edge_blocks=0)
+                 edge_blocks=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

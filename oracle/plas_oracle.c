@@ -38,8 +38,11 @@
  *     schedule uses the (non-squared) mean L2 distance;
  *   - blur: half-width r = floor(phi), sigma = sigma_ratio * phi, taps
  *     truncated at the grid border and renormalised by the in-range tap mass;
- *   - only full beta x beta blocks are re-assigned; the shift is drawn from
- *     [0, min(beta, side - beta + 1)) per axis so at least one block fits;
+ *   - every block that meets the grid is re-assigned, the blocks cut by the
+ *     grid border included (their groups whose four cells lie in the grid;
+ *     schedule.edge_blocks = 0 keeps whole blocks only); the shift is drawn
+ *     from [0, min(beta, side - beta + 1)) per axis, which is [0, beta)
+ *     whenever phi0 = min(H, W)/2 - 1;
  *   - the random sources are Philox4x32-10 (Salmon et al., SC'11) driving a
  *     six-round Feistel permutation with cycle walking;
  *   - ties between permutations: the first in lexicographic order wins;
@@ -157,10 +160,11 @@ typedef struct {
     int target_mode;    /* 0: Gaussian target (Sec. 3.1); 1: box target      */
     long long max_iters;/* stop after this many iterations in total; 0 = none */
     int edge_blocks;    /* reading of the borders after the shift (Sec. 3.1): */
-                        /* 0 (default) only whole blocks are re-assigned; 1  */
-                        /* the blocks cut by the grid border are too, each   */
-                        /* group of four whose cells all lie inside the grid */
-                        /* (the others stay put)                             */
+                        /* 1 (the default reading) every block that meets    */
+                        /* the grid is re-assigned, those cut by the grid    */
+                        /* border included: each of their groups of four     */
+                        /* whose cells all lie inside the grid (the others   */
+                        /* stay put); 0 only whole blocks                    */
     int pad_;
 } orc_schedule;
 
