@@ -97,6 +97,12 @@ typedef struct plas_schedule {
                         /* a barrier that waits 2 s gives up with            */
                         /* PLAS_ERR_TIMEOUT (the GPU stays usable).  The     */
                         /* concurrent server policy never uses it.           */
+    int whole_blocks;   /* 0 (default): every block that meets the grid is  */
+                        /* re-assigned, the blocks cut by the grid border    */
+                        /* included (their groups of four cells inside the   */
+                        /* grid; Sec. 3.1, the shifted blocks cover the      */
+                        /* whole grid).  1: whole blocks from the shift on   */
+                        /* only (the alternative reading)                    */
     int checked;        /* 1: checked run (plas_sort): 256-byte guard bands   */
                         /* between the workspace regions are filled with a   */
                         /* pattern and verified after the sort, and the      */

@@ -47,6 +47,7 @@ class Schedule:
     graphs: bool = True
     target_mode: int = 0  # 0 Gaussian target, 1 box target (fast low-pass variant)
     persistent: int = 0   # 1: one cooperative launch per batch of sweeps; 0 / -1: graph-replayed launches
+    whole_blocks: bool = False  # True: only whole blocks take part (not those cut by the border)
     checked: bool = False  # guard bands around workspace regions + device bounds checks
 
     def to_c(self, trace_S: Optional[torch.Tensor] = None,
@@ -60,6 +61,7 @@ class Schedule:
         s.target_mode = int(self.target_mode)
         s.persistent = int(self.persistent)
         s.checked = int(self.checked)
+        s.whole_blocks = int(self.whole_blocks)
         s.trace_S = trace_S.data_ptr() if trace_S is not None else None
         s.trace_level = trace_level.data_ptr() if trace_level is not None else None
         cap = 0

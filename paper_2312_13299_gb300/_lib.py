@@ -34,7 +34,7 @@ class plas_schedule(ctypes.Structure):
                 ("tol", c_double), ("sigma_ratio", c_double), ("min_block", c_int),
                 ("shuffle_init", c_int), ("normalize", c_int), ("iters_per_poll", c_int),
                 ("max_iters", c_ll), ("profile", c_int), ("graphs", c_int), ("target_mode", c_int),
-                ("persistent", c_int), ("checked", c_int),
+                ("persistent", c_int), ("whole_blocks", c_int), ("checked", c_int),
                 ("trace_S", c_void_p), ("trace_level", c_void_p), ("trace_cap", c_ll)]
 
 

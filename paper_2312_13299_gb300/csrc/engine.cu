@@ -177,6 +177,7 @@ class Engine {
         ref.target_mode = s_.target_mode;
         ref.sat = sl->ws.sat;
         ref.checked = s_.checked;
+        ref.edge_blocks = s_.whole_blocks ? 0 : 1;
         if (s_.checked) {
             launch_fill_guards(sl->ws.guards, st_);
             if (injected_guard_damage() && sl->ws.guards.n > 0)  // a planted overwrite (tests)
@@ -518,6 +519,7 @@ class Engine {
             r.target_mode = s_.target_mode;
             r.sat = sl->ws.sat;
             r.checked = s_.checked;
+            r.edge_blocks = s_.whole_blocks ? 0 : 1;
         }
         // the persistent sweep runs the medium FIR tiling, separate launches
         // the large one

@@ -485,6 +485,7 @@ static int target_impl(const float* x, int H, int W, int D, const float* weights
     ref.lv = ws.lv; ref.table = ws.table; ref.H = H; ref.W = W; ref.nlev = 1;
     ref.target_mode = mode;
     ref.sat = ws.sat;
+    ref.edge_blocks = 1;
     int rc = PLAS_OK;
     do {
         if (cudaMemcpyAsync(ws.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st) != cudaSuccess ||

@@ -77,6 +77,7 @@ struct GridRef {
     long long trace_cap;
     long long* sat;       // box target: N x round_up(D, 2) int64 summed-area table
     int checked;          // checked run: device bounds checks into the status word
+    int edge_blocks;      // 1: the blocks cut by the grid border take part (default)
 };
 
 // CTA -> grid map entry of a batched launch.

@@ -368,7 +368,8 @@ static __device__ void schedule_step(DevState* st, long long N, int nby, int nbx
     }
     st->d_last = d;
     st->it = it + 1;
-    st->grouped += (long long)nby * nbx * ngroups * 4;
+    // cells of the groups (with cut blocks an upper bound, capped at N)
+    st->grouped += std::min<long long>((long long)nby * nbx * ngroups * 4, N);
     if (st->level >= nlevels) st->done = 1;
     st->S = 0ull;
     st->arrivals = 0u;
@@ -400,7 +401,13 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
     const int beta = gr.lv[st->level].beta;
     int dy, dx;
     block_shift(gr.seed, st->epoch, beta, H, W, &dy, &dx);
-    const int nby = (H - dy) / beta, nbx = (W - dx) / beta;
+    // block origins (Sec. 3.1): every block that meets the grid, the ones cut
+    // by the top/left border included (edge reading, the default), or the
+    // whole blocks from (dy, dx) on
+    const bool edge = gr.edge_blocks != 0;
+    const int oy0 = edge && dy > 0 ? dy - beta : dy, ox0 = edge && dx > 0 ? dx - beta : dx;
+    const int nby = edge ? (H - oy0 + beta - 1) / beta : (H - dy) / beta;
+    const int nbx = edge ? (W - ox0 + beta - 1) / beta : (W - dx) / beta;
     const int ngroups = (beta * beta) / 4;
     // N <= 2^26 (checked on the host), so every cell and group index fits 32 bits
     const int ngt = nby * nbx * ngroups;
@@ -429,26 +436,32 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
         const uint32_t task = active ? (uint32_t)task0 : 0u;
         const uint32_t blk = task / (uint32_t)ngroups;
         const int by = (int)(blk / (uint32_t)nbx), bx = (int)(blk - (uint32_t)by * (uint32_t)nbx);
-        const int oy = dy + by * beta, ox = dx + bx * beta;
+        const int oy = oy0 + by * beta, ox = ox0 + bx * beta;
         const uint4 l4 = l4_next;
         if (base + nwarps * 8 < ngt)
             l4_next = ldg_ro<RO>(reinterpret_cast<const uint4*>(pi) + group_of(base + nwarps * 8));
         const uint32_t ls[4] = {l4.x, l4.y, l4.z, l4.w};
+        // cells of the group; a cell beyond the grid border (edge reading)
+        // reads cell 0 and takes no part: its group stays put
         int pos[4];
+        unsigned inmask = 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int ly = (int)(ls[k] / (uint32_t)beta);
             const int lx = (int)(ls[k] - (uint32_t)ly * (uint32_t)beta);
-            pos[k] = (oy + ly) * W + (ox + lx);
+            const int yy = oy + ly, xx = ox + lx;
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            inmask |= (unsigned)in << k;
+            pos[k] = in ? yy * W + xx : 0;
         }
+        const bool inside = inmask == 15u;
         if (CHECKED) {
             // checked run: every grouping entry must lie in the block and every
-            // cell in the grid; a violation is recorded and the warp's groups skipped
-            bool inb = true;
+            // cell position in the grid; a violation is recorded and the
+            // warp's groups skipped
+            bool inb = edge || inside;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                inb = inb && ls[k] < (uint32_t)(beta * beta) && pos[k] >= 0 && pos[k] < H * W &&
-                      oy + (int)(ls[k] / (uint32_t)beta) < H && ox + (int)(ls[k] % (uint32_t)beta) < W;
+            for (int k = 0; k < 4; ++k) inb = inb && ls[k] < (uint32_t)(beta * beta) && pos[k] >= 0 && pos[k] < H * W;
             if (!__all_sync(0xFFFFFFFFu, !active || inb)) {
                 if (active && !inb) atomicCAS(&st->status, 0, -7);  // PLAS_ERR_INTERNAL
                 continue;
@@ -497,23 +510,26 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
                 bp[n / 2] = bp[n - 1];
             }
         }
-        const int my_dst = (bp[0] >> (2 * qi)) & 3;
-        if (active) {
+        // a group with a cell beyond the border keeps its arrangement; each of
+        // its cells inside the grid adds its own distance
+        const int my_dst = inside ? (bp[0] >> (2 * qi)) & 3 : qi;
+        if (active && inside) {
             float4* dst = reinterpret_cast<float4*>(G + (size_t)pick4i(pos, my_dst) * GS);
 #pragma unroll
             for (int k = 0; k < GS / 4; ++k)
                 dst[k] = make_float4(grow[4 * k], grow[4 * k + 1], grow[4 * k + 2], grow[4 * k + 3]);
-            part += fixed_point(__fsqrt_rn(pick4(c, my_dst)), scale);
         }
+        if (active && ((inmask >> qi) & 1u)) part += fixed_point(__fsqrt_rn(pick4(c, my_dst)), scale);
     }
 
     // ---- cells outside the full blocks (enumerated directly: the rows above
     // and below the covered band, then the left and right margins of it) ----
+    // (none under the edge reading: the blocks cover the grid)
     const int cy0 = dy, cy1 = dy + nby * beta, cx0 = dx, cx1 = dx + nbx * beta;
     const int gthread = cr.local * kAssignThreads + (int)threadIdx.x;
     const int nthreads = cr.count * kAssignThreads;
     const int n_top = cy0 * W, n_bot = (H - cy1) * W, margin = W - (cx1 - cx0);
-    const int n_unc = n_top + n_bot + (cy1 - cy0) * margin;
+    const int n_unc = edge ? 0 : n_top + n_bot + (cy1 - cy0) * margin;
     for (int e = gthread; e < n_unc; e += nthreads) {
         int y, x;
         if (e < n_top + n_bot) {
@@ -541,7 +557,9 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
         const int by = (int)((uint32_t)blk / (uint32_t)nbx), bx = blk - by * nbx;
         const uint32_t l = pi[m];
         const int ly = (int)(l / (uint32_t)beta), lx = (int)(l - (uint32_t)ly * (uint32_t)beta);
-        const int p = (dy + by * beta + ly) * W + (dx + bx * beta + lx);
+        const int yy = oy0 + by * beta + ly, xx = ox0 + bx * beta + lx;
+        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;  // (edge reading)
+        const int p = yy * W + xx;
         float grow[GS], trow[TS];
         load_row4_rw<GS / 4>(G + (size_t)p * GS, grow);
         load_row4<TS / 4, RO>(T + (size_t)p * TS, trow);

@@ -141,6 +141,20 @@ def test_full_sort_ragged_and_degenerate(plas, orc, H, W, D, seed):
     _compare_full(plas, orc, x, H, W, seed)
 
 
+@pytest.mark.parametrize("H,W,D,seed", [(37, 53, 3, 1), (48, 80, 14, 2), (64, 64, 3, 0)])
+def test_full_sort_whole_blocks_reading(plas, orc, H, W, D, seed):
+    """The alternative reading of the shifted blocks (whole blocks only, the
+    blocks cut by the grid border left out) on both sides: bit-exact."""
+    x = np.random.default_rng(seed + 40).random((H * W, D), dtype=np.float32)
+    want = orc.sort(x, H, W, seed=seed, sched=orc.default_schedule(edge_blocks=0))
+    got = plas.sort(_cuda(x), H, W, seed=seed, schedule=plas.Schedule(whole_blocks=True),
+                    trace_cap=1 << 15)
+    assert np.array_equal(got.perm.cpu().numpy(), want["perm"])
+    n = want["iterations"]
+    assert got.state["it"] == n
+    assert np.array_equal(got.trace_S.cpu().numpy(), want["trace_S"])
+
+
 def test_full_sort_weights_unnormalized_and_no_shuffle(plas, orc):
     rng = np.random.default_rng(11)
     x = (rng.normal(size=(40 * 44, 6)) * [1, 5, 0.1, 2, 3, 1]).astype(np.float32)
