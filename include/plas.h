@@ -504,7 +504,7 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   PLAS_ERR_INVALID_ARG for unsupported sizes.
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
- *   shape on the current device would use (the defaults 8, 96 and 8 when
+ *   shape on the current device would use (the defaults 8, 96 and 4 when
  *   nothing is installed).  A radius r takes the direct kernel when
  *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
  *   the 128-row one, which streams with tensor copies when large_tma is 1

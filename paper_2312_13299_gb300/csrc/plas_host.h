@@ -90,7 +90,7 @@ size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 constexpr int kDirectTuneMaxR = 32;  // the tuner times the direct FIR kernel up to this radius
 constexpr int kDefaultSmallBelow = 8;
 constexpr int kDefaultMediumBelow = 96;
-constexpr int kDefaultAssignPerSm = 8;
+constexpr int kDefaultAssignPerSm = 4;
 struct Tuning {
     int small_below = kDefaultSmallBelow;    // direct FIR kernel (no ring) below this radius
     int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row

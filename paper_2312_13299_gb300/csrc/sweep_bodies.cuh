@@ -66,6 +66,14 @@ __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// 16-byte copy global -> shared through L2 only (data read once); with
+// take = false the destination is zero-filled and nothing is read
+__device__ __forceinline__ void cp_async_cg16(float4* sdst, const float* gsrc, bool take) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc),
+                 "r"(take ? 16 : 0)
+                 : "memory");
+}
 
 
 template <class TL>
@@ -417,7 +425,18 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
     const uint32_t* __restrict__ pi = gr.pi;
     unsigned long long part = 0ull;
 
-    const int lane = threadIdx.x & 31, qi = lane & 3, qbase = lane & ~3;
+    const int lane = threadIdx.x & 31, qi = lane & 3, qbase = lane & ~3, q = lane >> 2;
+    // Row staging (up to 16 channels): per warp, the 32 grid rows of its 8
+    // quads at an odd stride of SG float4s, and the 32 target rows at an odd
+    // stride ST with one float4 between quads, so that the shared-memory reads
+    // below (lane i: grid row i of its quad; the quad: one target row) are
+    // free of bank conflicts.
+    constexpr bool kStaged = D <= 16;
+    constexpr int NG = GS / 4, NT = TS / 4, SG = NG | 1, ST = NT | 1, QT = 4 * ST + 1;
+    constexpr int kWarpStage = 32 * SG + 8 * QT;
+    __shared__ float4 s_stage[kStaged ? (kAssignThreads / 32) * kWarpStage : 1];
+    float4* const sg = s_stage + (kStaged ? (int)(threadIdx.x >> 5) * kWarpStage : 0);
+    float4* const stt = sg + 32 * SG;
     const int gwarp = (cr.local * kAssignThreads + (int)threadIdx.x) >> 5;
     const int nwarps = (cr.count * kAssignThreads) >> 5;
     constexpr Perm24 kPerm24 = make_perm24();
@@ -467,14 +486,71 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
                 continue;
             }
         }
-        float grow[GS];
-        load_row4_rw<GS / 4>(G + (size_t)pick4i(pos, qi) * GS, grow);
         float c[4];
+        float grow[GS];  // the lane's own grid row (all of it without staging)
+        if (kStaged) {
+            // the quad copies its four grid rows and four target rows into the
+            // warp's staging area, lane qi taking float4s qi, qi + 4, ... of
+            // the rows laid end to end, so every copy instruction moves whole
+            // 64-byte rows (one memory transaction per row, not per lane).
+            // Rows of cells beyond the border (and of idle quads) are
+            // zero-filled without a read: their costs are never used.
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+            for (int m = 0; m < NG; ++m) {
+                const int e = qi + 4 * m, row = e / NG, col = e - row * NG;
+                cp_async_cg16(sg + (4 * q + row) * SG + col,
+                              G + (size_t)pick4i(pos, row) * GS + 4 * col,
+                              active && ((inmask >> row) & 1u));
+            }
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+                const int e = qi + 4 * m, row = e / NT, col = e - row * NT;
+                cp_async_cg16(stt + q * QT + row * ST + col,
+                              T + (size_t)pick4i(pos, row) * TS + 4 * col,
+                              active && ((inmask >> row) & 1u));
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            // cost row qi, ascending channels: c[j] = sum_d (g_d - t_j,d)^2
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+                const float4 v = sg[(4 * q + qi) * SG + k];
+                grow[4 * k] = v.x; grow[4 * k + 1] = v.y; grow[4 * k + 2] = v.z; grow[4 * k + 3] = v.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float trow[TS];
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    const float4 v = stt[q * QT + j * ST + k];
+                    trow[4 * k] = v.x; trow[4 * k + 1] = v.y; trow[4 * k + 2] = v.z; trow[4 * k + 3] = v.w;
+                }
+                c[j] = sqdist<D>(grow, trow);
+            }
+        } else {
+            // lane qi loads the grid row and the target row of its own cell;
+            // the quad passes the target rows around with shuffles
             float trow[TS];
-            load_row4<TS / 4, RO>(T + (size_t)pos[j] * TS, trow);
-            c[j] = sqdist<D>(grow, trow);
+            const int mypos = pick4i(pos, qi);
+            load_row4_rw<GS / 4>(G + (size_t)mypos * GS, grow);
+            load_row4<TS / 4, RO>(T + (size_t)mypos * TS, trow);
+            // cost row qi, ascending channels: cr[m] = sum_d (g_d - t_d)^2
+            // against the target row of lane (qi + m) & 3 of the quad
+            float cr[4];
+            cr[0] = sqdist<D>(grow, trow);
+#pragma unroll
+            for (int m = 1; m < 4; ++m) {
+                const int src = qbase | ((qi + m) & 3);
+                float acc = 0.0f;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float delta = __fsub_rn(grow[d], __shfl_sync(0xFFFFFFFFu, trow[d], src));
+                    acc = __fmaf_rn(delta, delta, acc);
+                }
+                cr[m] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[j] = pick4(cr, (j - qi) & 3);
         }
         // all-gather the cost matrix inside the quad; every lane then scores
         // all 24 permutations (identical result in the four lanes)
@@ -483,37 +559,54 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) C[i][j] = __shfl_sync(0xFFFFFFFFu, c[j], qbase | i);
-        // first strict minimum in lexicographic order, as a pairwise tree:
-        // the left operand always holds the earlier permutations and wins
-        // ties, so the tree picks the same permutation as a sequential scan.
-        // Each node carries its permutation packed as four 2-bit targets.
-        float bc[24];
-        int bp[24];
+        // first strict minimum in lexicographic order: four running minima,
+        // one per first target a (permutations 6a..6a+5, scanned in order
+        // with a strict <), merged in the order of a with a strict < as
+        // well, which is the sequential scan's choice.  Each minimum carries
+        // its permutation packed as four 2-bit targets.
+        float best[4];
+        int bcode[4];
 #pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            bc[k] = __fadd_rn(__fadd_rn(__fadd_rn(C[0][kPerm24.p[k][0]], C[1][kPerm24.p[k][1]]),
-                                        C[2][kPerm24.p[k][2]]),
-                              C[3][kPerm24.p[k][3]]);
-            bp[k] = kPerm24.p[k][0] | (kPerm24.p[k][1] << 2) | (kPerm24.p[k][2] << 4) |
-                    (kPerm24.p[k][3] << 6);
-        }
+        for (int a = 0; a < 4; ++a) {
 #pragma unroll
-        for (int n = 24; n > 1; n = (n + 1) / 2) {
-#pragma unroll
-            for (int m = 0; m < n / 2; ++m) {
-                const bool right = bc[2 * m + 1] < bc[2 * m];
-                bc[m] = right ? bc[2 * m + 1] : bc[2 * m];
-                bp[m] = right ? bp[2 * m + 1] : bp[2 * m];
+            for (int k = 6 * a; k < 6 * a + 6; ++k) {
+                const float s = __fadd_rn(
+                    __fadd_rn(__fadd_rn(C[0][kPerm24.p[k][0]], C[1][kPerm24.p[k][1]]),
+                              C[2][kPerm24.p[k][2]]),
+                    C[3][kPerm24.p[k][3]]);
+                const int code = kPerm24.p[k][0] | (kPerm24.p[k][1] << 2) |
+                                 (kPerm24.p[k][2] << 4) | (kPerm24.p[k][3] << 6);
+                if (k == 6 * a || s < best[a]) {
+                    best[a] = s;
+                    bcode[a] = code;
+                }
             }
-            if (n & 1) {
-                bc[n / 2] = bc[n - 1];
-                bp[n / 2] = bp[n - 1];
+        }
+        int bp0 = bcode[0];
+        float b0 = best[0];
+#pragma unroll
+        for (int a = 1; a < 4; ++a) {
+            if (best[a] < b0) {
+                b0 = best[a];
+                bp0 = bcode[a];
             }
         }
         // a group with a cell beyond the border keeps its arrangement; each of
         // its cells inside the grid adds its own distance
-        const int my_dst = inside ? (bp[0] >> (2 * qi)) & 3 : qi;
-        if (active && inside) {
+        const int my_dst = inside ? (bp0 >> (2 * qi)) & 3 : qi;
+        if (kStaged) {
+            // the quad writes its staged rows back whole: row j moves to cell
+            // pos[sigma(j)], lane qi taking the same float4s as in the copy
+            if (active && inside) {
+#pragma unroll
+                for (int m = 0; m < NG; ++m) {
+                    const int e = qi + 4 * m, row = e / NG, col = e - row * NG;
+                    const int dst = pick4i(pos, (bp0 >> (2 * row)) & 3);
+                    reinterpret_cast<float4*>(G + (size_t)dst * GS)[col] = sg[(4 * q + row) * SG + col];
+                }
+            }
+            __syncwarp();  // the stage is refilled by the next iteration
+        } else if (active && inside) {
             float4* dst = reinterpret_cast<float4*>(G + (size_t)pick4i(pos, my_dst) * GS);
 #pragma unroll
             for (int k = 0; k < GS / 4; ++k)

@@ -44,7 +44,7 @@ def test_library_is_sm103a_only():
 
 
 # (fir_small_below, fir_medium_below, assign_ctas_per_sm) when nothing is installed
-DEFAULT_TUNING = (8, 96, 8)
+DEFAULT_TUNING = (8, 96, 4)
 
 
 def test_tuning_table_round_trip_host_only():
@@ -66,4 +66,4 @@ def test_tuning_table_round_trip_host_only():
             plas.set_tuning(64, 64, 5, fir_medium_below=-1)
     finally:
         plas.set_tuning(64, 64, 5)
-    assert plas.get_tuning(64, 64, 5)["assign_ctas_per_sm"] == 8
+    assert plas.get_tuning(64, 64, 5)["assign_ctas_per_sm"] == DEFAULT_TUNING[2]
