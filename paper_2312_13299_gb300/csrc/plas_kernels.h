@@ -103,16 +103,23 @@ __device__ __forceinline__ CtaRef resolve_cta(const CtaMap* __restrict__ map) {
 // The grouping permutation of the current iteration (Sec. 3.1: one random
 // permutation of the beta^2 block cells, shared by all blocks), pi[m] for
 // m < beta^2, spread over 'count' CTAs of 'threads' threads (this CTA is
-// number 'local').  The assignment launch that follows reads it.
+// number 'local').  The assignment launch that follows reads it.  Entry m
+// holds the block cell l = pi(m) already split into its row and column,
+// (l / beta) << 16 | (l % beta) (beta <= 8192), so the assignment divides
+// nothing.
 __device__ __forceinline__ void write_group_table(const GridRef& gr, const LevelDesc& lv,
                                                   const DevState* st, int local, int count,
                                                   int threads) {
-    const uint32_t n = (uint32_t)lv.beta * (uint32_t)lv.beta;
+    const uint32_t beta = (uint32_t)lv.beta;
+    const uint32_t n = beta * beta;
     const uint32_t h = feistel_half_bits(n);
     const uint64_t it = (uint64_t)st->it;
     const uint32_t stride = (uint32_t)count * (uint32_t)threads;
-    for (uint32_t m = (uint32_t)local * (uint32_t)threads + threadIdx.x; m < n; m += stride)
-        gr.pi[m] = keyed_permute(m, n, h, gr.seed, kTagGroup, it);
+    for (uint32_t m = (uint32_t)local * (uint32_t)threads + threadIdx.x; m < n; m += stride) {
+        const uint32_t l = keyed_permute(m, n, h, gr.seed, kTagGroup, it);
+        const uint32_t ly = l / beta;
+        gr.pi[m] = (ly << 16) | (l - ly * beta);
+    }
 }
 
 // Cell strides of the working grid G (features + index, padded to float4) and

@@ -338,6 +338,46 @@ __device__ __forceinline__ int pick4i(const int (&v)[4], int j) {
     return j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
 }
 
+// The six permutations that send cell 0 to target a are numbers 6a..6a+5 of
+// the lexicographic order; with r0 < r1 < r2 the other three targets they
+// send cells 1, 2, 3 to (r0 r1 r2), (r0 r2 r1), (r1 r0 r2), (r1 r2 r0),
+// (r2 r0 r1), (r2 r1 r0): kRest6[w] indexes (r0, r1, r2) for permutation
+// 6a + w.  kKeys[a] packs the lexicographic keys (targets of cells 0..3 as
+// base-4 digits, cell 0 most significant) of those six permutations, eight
+// bits each.
+__device__ constexpr int kRest6[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2},
+                                         {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+struct PermKeys {
+    unsigned long long k[4];
+};
+__host__ __device__ constexpr PermKeys make_perm_keys() {
+    PermKeys t{};
+    const Perm24 p = make_perm24();
+    for (int a = 0; a < 4; ++a)
+        for (int w = 0; w < 6; ++w) {
+            const int* q = p.p[6 * a + w];
+            const unsigned long long key =
+                (unsigned long long)((q[0] << 6) | (q[1] << 4) | (q[2] << 2) | q[3]);
+            t.k[a] |= key << (8 * w);
+        }
+    return t;
+}
+// compile-time check of the layout above against the lexicographic table
+__host__ __device__ constexpr bool perm_split_ok() {
+    const Perm24 p = make_perm24();
+    constexpr int rest6[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int a = 0; a < 4; ++a) {
+        const int r[3] = {a == 0 ? 1 : 0, a <= 1 ? 2 : 1, a <= 2 ? 3 : 2};
+        for (int w = 0; w < 6; ++w) {
+            if (p.p[6 * a + w][0] != a) return false;
+            for (int m = 0; m < 3; ++m)
+                if (p.p[6 * a + w][m + 1] != r[rest6[w][m]]) return false;
+        }
+    }
+    return true;
+}
+static_assert(perm_split_ok(), "permutations 6a..6a+5 are (a, rest in lexicographic order)");
+
 // Schedule step (Sec. 3.1): d = mean L2 distance to the target; an assignment
 // that improves d by less than tol (relative) is a stall; one stall draws a
 // new block shift, a second in a row shrinks the radius; the sort ends when
@@ -439,26 +479,43 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
     float4* const stt = sg + 32 * SG;
     const int gwarp = (cr.local * kAssignThreads + (int)threadIdx.x) >> 5;
     const int nwarps = (cr.count * kAssignThreads) >> 5;
-    constexpr Perm24 kPerm24 = make_perm24();
+    constexpr PermKeys kPermKeys = make_perm_keys();
     // ---- groups: 8 per warp ----
-    // the grouping-table entries of the next iteration are read one iteration
-    // ahead, so each iteration waits for one memory round trip, not two
-    auto group_of = [&](int b) -> int {
-        const int t = b + (lane >> 2);
-        return t < ngt ? (int)((uint32_t)t % (uint32_t)ngroups) : 0;
-    };
+    // Lane cursor: the lane's group task = (by * nbx + bx) * ngroups + g is
+    // advanced by S = 8 * nwarps per step without dividing: S splits once
+    // into whole blocks and a remainder.  The grouping-table entries of the
+    // next step are read one step ahead, so each step waits for one memory
+    // round trip, not two.
+    const uint32_t ug = (uint32_t)ngroups, unbx = (uint32_t)nbx;
+    const uint32_t S = (uint32_t)nwarps * 8u;
+    const uint32_t Sg = S % ug, Sb = S / ug, Sbx = Sb % unbx, Sby = Sb / unbx;
+    uint32_t cg, cbx, cby;
+    {
+        const uint32_t t = (uint32_t)(gwarp * 8 + (lane >> 2)), b = t / ug;
+        cg = t - b * ug;
+        cby = b / unbx;
+        cbx = b - cby * unbx;
+    }
+    const uint4* __restrict__ pi4 = reinterpret_cast<const uint4*>(pi);
     uint4 l4_next = make_uint4(0u, 0u, 0u, 0u);
-    if (gwarp * 8 < ngt) l4_next = ldg_ro<RO>(reinterpret_cast<const uint4*>(pi) + group_of(gwarp * 8));
+    if (gwarp * 8 < ngt) l4_next = ldg_ro<RO>(pi4 + cg);  // cg < ngroups always
+#pragma unroll 1
     for (int base = gwarp * 8; base < ngt; base += nwarps * 8) {
-        const int task0 = base + (lane >> 2);
-        const bool active = task0 < ngt;
-        const uint32_t task = active ? (uint32_t)task0 : 0u;
-        const uint32_t blk = task / (uint32_t)ngroups;
-        const int by = (int)(blk / (uint32_t)nbx), bx = (int)(blk - (uint32_t)by * (uint32_t)nbx);
-        const int oy = oy0 + by * beta, ox = ox0 + bx * beta;
+        const bool active = base + (lane >> 2) < ngt;
+        const int oy = oy0 + (int)cby * beta, ox = ox0 + (int)cbx * beta;
         const uint4 l4 = l4_next;
-        if (base + nwarps * 8 < ngt)
-            l4_next = ldg_ro<RO>(reinterpret_cast<const uint4*>(pi) + group_of(base + nwarps * 8));
+        {
+            cg += Sg;
+            const uint32_t carry = cg >= ug ? 1u : 0u;
+            cg -= carry ? ug : 0u;
+            cbx += Sbx + carry;
+            if (cbx >= unbx) {
+                cbx -= unbx;
+                cby += 1u;
+            }
+            cby += Sby;
+        }
+        if (base + nwarps * 8 < ngt) l4_next = ldg_ro<RO>(pi4 + cg);
         const uint32_t ls[4] = {l4.x, l4.y, l4.z, l4.w};
         // cells of the group; a cell beyond the grid border (edge reading)
         // reads cell 0 and takes no part: its group stays put
@@ -466,9 +523,7 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
         unsigned inmask = 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int ly = (int)(ls[k] / (uint32_t)beta);
-            const int lx = (int)(ls[k] - (uint32_t)ly * (uint32_t)beta);
-            const int yy = oy + ly, xx = ox + lx;
+            const int yy = oy + (int)(ls[k] >> 16), xx = ox + (int)(ls[k] & 0xFFFFu);
             const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
             inmask |= (unsigned)in << k;
             pos[k] = in ? yy * W + xx : 0;
@@ -480,7 +535,7 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
             // warp's groups skipped
             bool inb = edge || inside;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) inb = inb && ls[k] < (uint32_t)(beta * beta) && pos[k] >= 0 && pos[k] < H * W;
+            for (int k = 0; k < 4; ++k) inb = inb && (ls[k] >> 16) < (uint32_t)beta && (ls[k] & 0xFFFFu) < (uint32_t)beta && pos[k] >= 0 && pos[k] < H * W;
             if (!__all_sync(0xFFFFFFFFu, !active || inb)) {
                 if (active && !inb) atomicCAS(&st->status, 0, -7);  // PLAS_ERR_INTERNAL
                 continue;
@@ -552,48 +607,51 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
 #pragma unroll
             for (int j = 0; j < 4; ++j) c[j] = pick4(cr, (j - qi) & 3);
         }
-        // all-gather the cost matrix inside the quad; every lane then scores
-        // all 24 permutations (identical result in the four lanes)
+        // all-gather the cost matrix inside the quad
         float C[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) C[i][j] = __shfl_sync(0xFFFFFFFFu, c[j], qbase | i);
-        // first strict minimum in lexicographic order: four running minima,
-        // one per first target a (permutations 6a..6a+5, scanned in order
-        // with a strict <), merged in the order of a with a strict < as
-        // well, which is the sequential scan's choice.  Each minimum carries
-        // its permutation packed as four 2-bit targets.
-        float best[4];
-        int bcode[4];
+        // lane qi scores the six permutations that send cell 0 to target qi
+        // (kRest6), keeping the first strict minimum; the quad then takes the
+        // lowest cost, on equal costs the lowest lexicographic key, which is
+        // the first strict minimum over all 24 in lexicographic order
+        float x[4][3];  // x[i][m] = C[i][r_m], the targets other than qi in order
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int i = 1; i < 4; ++i) {
+            x[i][0] = qi == 0 ? C[i][1] : C[i][0];
+            x[i][1] = qi <= 1 ? C[i][2] : C[i][1];
+            x[i][2] = qi <= 2 ? C[i][3] : C[i][2];
+        }
+        const float c0 = pick4(C[0], qi);
+        float best = 0.0f;
+        int bw = 0;
 #pragma unroll
-            for (int k = 6 * a; k < 6 * a + 6; ++k) {
-                const float s = __fadd_rn(
-                    __fadd_rn(__fadd_rn(C[0][kPerm24.p[k][0]], C[1][kPerm24.p[k][1]]),
-                              C[2][kPerm24.p[k][2]]),
-                    C[3][kPerm24.p[k][3]]);
-                const int code = kPerm24.p[k][0] | (kPerm24.p[k][1] << 2) |
-                                 (kPerm24.p[k][2] << 4) | (kPerm24.p[k][3] << 6);
-                if (k == 6 * a || s < best[a]) {
-                    best[a] = s;
-                    bcode[a] = code;
-                }
+        for (int w = 0; w < 6; ++w) {
+            const float sc = __fadd_rn(
+                __fadd_rn(__fadd_rn(c0, x[1][kRest6[w][0]]), x[2][kRest6[w][1]]),
+                x[3][kRest6[w][2]]);
+            if (w == 0 || sc < best) {
+                best = sc;
+                bw = w;
             }
         }
-        int bp0 = bcode[0];
-        float b0 = best[0];
+        const unsigned long long keys =
+            qi == 0 ? kPermKeys.k[0] : (qi == 1 ? kPermKeys.k[1] : (qi == 2 ? kPermKeys.k[2] : kPermKeys.k[3]));
+        unsigned key = (unsigned)(keys >> (8 * bw)) & 0xFFu;
 #pragma unroll
-        for (int a = 1; a < 4; ++a) {
-            if (best[a] < b0) {
-                b0 = best[a];
-                bp0 = bcode[a];
+        for (int off = 1; off < 4; off <<= 1) {
+            const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+            const unsigned okey = __shfl_xor_sync(0xFFFFFFFFu, key, off);
+            if (ob < best || (ob == best && okey < key)) {
+                best = ob;
+                key = okey;
             }
         }
         // a group with a cell beyond the border keeps its arrangement; each of
         // its cells inside the grid adds its own distance
-        const int my_dst = inside ? (bp0 >> (2 * qi)) & 3 : qi;
+        const int my_dst = inside ? (int)(key >> (6 - 2 * qi)) & 3 : qi;
         if (kStaged) {
             // the quad writes its staged rows back whole: row j moves to cell
             // pos[sigma(j)], lane qi taking the same float4s as in the copy
@@ -601,7 +659,7 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
 #pragma unroll
                 for (int m = 0; m < NG; ++m) {
                     const int e = qi + 4 * m, row = e / NG, col = e - row * NG;
-                    const int dst = pick4i(pos, (bp0 >> (2 * row)) & 3);
+                    const int dst = pick4i(pos, (int)(key >> (6 - 2 * row)) & 3);
                     reinterpret_cast<float4*>(G + (size_t)dst * GS)[col] = sg[(4 * q + row) * SG + col];
                 }
             }
@@ -623,6 +681,7 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
     const int nthreads = cr.count * kAssignThreads;
     const int n_top = cy0 * W, n_bot = (H - cy1) * W, margin = W - (cx1 - cx0);
     const int n_unc = edge ? 0 : n_top + n_bot + (cy1 - cy0) * margin;
+#pragma unroll 1
     for (int e = gthread; e < n_unc; e += nthreads) {
         int y, x;
         if (e < n_top + n_bot) {
@@ -644,12 +703,13 @@ __device__ __forceinline__ void assign_body(const GridRef* __restrict__ grids, c
     // ---- leftover cells of each block (beta^2 mod 4 of them) ----
     const int nleft = beta * beta - 4 * ngroups;
     const int nl = nby * nbx * nleft;
+#pragma unroll 1
     for (int e = gthread; e < nl; e += nthreads) {
         const int blk = (int)((uint32_t)e / (uint32_t)nleft);
         const int m = 4 * ngroups + (e - blk * nleft);
         const int by = (int)((uint32_t)blk / (uint32_t)nbx), bx = blk - by * nbx;
         const uint32_t l = pi[m];
-        const int ly = (int)(l / (uint32_t)beta), lx = (int)(l - (uint32_t)ly * (uint32_t)beta);
+        const int ly = (int)(l >> 16), lx = (int)(l & 0xFFFFu);
         const int yy = oy0 + by * beta + ly, xx = ox0 + bx * beta + lx;
         if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;  // (edge reading)
         const int p = yy * W + xx;
