@@ -505,10 +505,13 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
  *   shape on the current device would use (the defaults 8, 96 and 4 when
- *   nothing is installed).  A radius r takes the direct kernel when
- *   r < fir_small_below, else the 64-row one when r < fir_medium_below, else
- *   the 128-row one, which streams with tensor copies when large_tma is 1
- *   and the grid allows it.  Thread-safe.
+ *   nothing is installed).  A radius r takes the small-radius path when
+ *   r < fir_small_below (both passes in one launch when small_fused is 1,
+ *   r <= 11 and D <= 16; otherwise the direct kernel), else the 64-row one
+ *   when r < fir_medium_below, else the 128-row one, which streams with
+ *   tensor copies when large_tma is 1 and the grid allows it.  plas_autotune
+ *   times the one-launch kernel for the small path where it applies.
+ *   Thread-safe.
  */
 #define PLAS_TUNE_MAX_RADII 16
 #define PLAS_TUNE_ASSIGN_CANDIDATES 4
@@ -531,6 +534,11 @@ typedef struct plas_tuning {
     float fir_large_ring_us[PLAS_TUNE_MAX_RADII]; /* both passes, chunked    */
     float fir_large_tma_us[PLAS_TUNE_MAX_RADII];  /* both passes, tensor      */
                                                   /* copies; -1: not eligible */
+    int small_fused;        /* 1: radii of the small path up to 11, with at    */
+                            /* most 16 channels, run both passes in one launch */
+                            /* (the pass along y into shared memory, then the  */
+                            /* pass along x); 0: the direct kernel, two        */
+                            /* launches.  Same bits.  Default 1                */
 } plas_tuning;
 int plas_autotune(int H, int W, int D, void* stream, plas_tuning* out);
 int plas_set_tuning(int H, int W, int D, const plas_tuning* t /* host or NULL */);

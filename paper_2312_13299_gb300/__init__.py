@@ -279,7 +279,8 @@ def _tuning_dict(t: "_lib.plas_tuning") -> dict:
             "assign_us": [round(v, 2) for v in t.assign_us] if n else [],
             "large_tma": int(t.large_tma),
             "fir_large_ring_us": [round(v, 2) for v in t.fir_large_ring_us[:n]],
-            "fir_large_tma_us": [round(v, 2) for v in t.fir_large_tma_us[:n]]}
+            "fir_large_tma_us": [round(v, 2) for v in t.fir_large_tma_us[:n]],
+            "small_fused": int(t.small_fused)}
 
 
 def autotune(H: int, W: int, D: int, device=None) -> dict:
@@ -296,14 +297,16 @@ def autotune(H: int, W: int, D: int, device=None) -> dict:
 
 def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
                assign_ctas_per_sm: Optional[int] = None,
-               fir_medium_below: Optional[int] = None, large_tma: Optional[bool] = None) -> None:
+               fir_medium_below: Optional[int] = None, large_tma: Optional[bool] = None,
+               small_fused: Optional[bool] = None) -> None:
     """Install launch shapes for (H, W, D) on the current device; with every
     argument None the entry is removed (defaults apply again).  A radius r
-    takes the direct FIR kernel when r < fir_small_below, else the 64-row one
-    when r < fir_medium_below, else the 128-row one (with tensor copies when
-    large_tma is set and the grid allows it)."""
+    takes the small-radius path when r < fir_small_below (both passes in one
+    launch when small_fused is set, r <= 11 and D <= 16, else the direct
+    kernel), else the 64-row one when r < fir_medium_below, else the 128-row
+    one (with tensor copies when large_tma is set and the grid allows it)."""
     if (fir_small_below is None and assign_ctas_per_sm is None and fir_medium_below is None
-            and large_tma is None):
+            and large_tma is None and small_fused is None):
         check(load().plas_set_tuning(H, W, D, None), "plas_set_tuning")
         return
     cur = get_tuning(H, W, D)
@@ -313,6 +316,7 @@ def set_tuning(H: int, W: int, D: int, fir_small_below: Optional[int] = None,
     t.assign_ctas_per_sm = (cur["assign_ctas_per_sm"] if assign_ctas_per_sm is None
                             else assign_ctas_per_sm)
     t.large_tma = cur["large_tma"] if large_tma is None else int(bool(large_tma))
+    t.small_fused = cur["small_fused"] if small_fused is None else int(bool(small_fused))
     check(load().plas_set_tuning(H, W, D, ctypes.byref(t)), "plas_set_tuning")
 
 

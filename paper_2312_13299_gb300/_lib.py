@@ -78,7 +78,7 @@ class plas_tuning(ctypes.Structure):
                 ("assign_per_sm", c_int * TUNE_ASSIGN_CANDIDATES),
                 ("assign_us", c_float * TUNE_ASSIGN_CANDIDATES), ("large_tma", c_int),
                 ("fir_large_ring_us", c_float * TUNE_MAX_RADII),
-                ("fir_large_tma_us", c_float * TUNE_MAX_RADII)]
+                ("fir_large_tma_us", c_float * TUNE_MAX_RADII), ("small_fused", c_int)]
 
 
 P = ctypes.POINTER

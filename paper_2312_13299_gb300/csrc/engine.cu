@@ -232,9 +232,9 @@ class Engine {
         if (one) {
             const Slot* sl = active_[0];
             const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
-            p.var = fir_tiling(sl->geo.lv[L].r, sl->tune);
-            p.ctas[kClsFirY] = fir_ctas(sl->job.H, sl->job.W * D_, p.var);
-            p.ctas[kClsFirX] = fir_ctas(sl->job.W, sl->job.H * D_, p.var);
+            p.var = fir_variant(sl->geo.lv[L].r, D_, sl->tune);
+            p.ctas[kClsFirY] = fir_pass_ctas(0, sl->job.H, sl->job.W, D_, p.var);
+            p.ctas[kClsFirX] = fir_pass_ctas(1, sl->job.H, sl->job.W, D_, p.var);
         }
         if (one) persist_ = want_persist();
         if (persist_) {
@@ -801,10 +801,13 @@ extern "C" int plas_sort(const float* x, int H, int W, int D, const float* weigh
                 const double its = (double)(fin.it - (resume ? state_io->it : 0));
                 stats->kernel[PLAS_K_PREP].bytes = (double)N * D * 8 + (double)N * grid_stride(D) * 4;
                 // target: read the features, write the target (8 N D bytes per
-                // iteration); the Gaussian takes two passes, each counted in full
+                // iteration); the Gaussian takes two passes, each counted in full,
+                // except in iterations whose pass-0 launch ran both passes (fused
+                // small-radius kernel): their work is all in BLUR_COLS
                 stats->kernel[PLAS_K_BLUR_COLS].bytes = its * 8.0 * (double)N * D;
-                stats->kernel[PLAS_K_BLUR_COLS].flops = 2.0 * fin.fmas_y;
-                stats->kernel[PLAS_K_BLUR_ROWS].bytes = s.target_mode == 1 ? 0.0 : its * 8.0 * (double)N * D;
+                stats->kernel[PLAS_K_BLUR_COLS].flops = 2.0 * (fin.fmas_y + fin.fmas_xf);
+                stats->kernel[PLAS_K_BLUR_ROWS].bytes =
+                    s.target_mode == 1 ? 0.0 : (its - (double)fin.fused_its) * 8.0 * (double)N * D;
                 stats->kernel[PLAS_K_BLUR_ROWS].flops = 2.0 * fin.fmas_x;
                 // the grouping table is written by the pass-0 launches
                 stats->kernel[PLAS_K_BLUR_COLS].bytes += 4.0 * fin.beta2_sum;
@@ -897,11 +900,15 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
                 out->fir_large_tma_us[i] = us;
                 continue;
             }
-            const int c0 = fir_ctas(H, W * D, var), c1 = fir_ctas(W, H * D, var);
+            // the small-radius path: the one-launch kernel where it applies
+            Tuning small_only;
+            small_only.small_below = r + 1;
+            const int kv = var == kFirSmallRadius ? fir_variant(r, D, small_only) : var;
+            const int c0 = fir_pass_ctas(0, H, W, D, kv), c1 = fir_pass_ctas(1, H, W, D, kv);
             float us = 0.0f;
             if (int e = time_us(st, a, b, kReps, [&] {
-                    launch_fir(0, sl.ws.ref, nullptr, c0, D, var, st);
-                    launch_fir(1, sl.ws.ref, nullptr, c1, D, var, st);
+                    launch_fir(0, sl.ws.ref, nullptr, c0, D, kv, st);
+                    launch_fir(1, sl.ws.ref, nullptr, c1, D, kv, st);
                 }, &us))
                 return e;
             (var == kFirSmallRadius ? out->fir_small_us
@@ -965,6 +972,7 @@ int autotune_run(int H, int W, int D, cudaStream_t st, float* x, char* ws, cudaE
     out->fir_medium_below = best.medium_below;
     out->assign_ctas_per_sm = per_sm[best_c];
     out->large_tma = large_tma;
+    out->small_fused = 1;
     Tuning tu = best;
     tu.assign_per_sm = per_sm[best_c];
     tu.large_tma = large_tma;

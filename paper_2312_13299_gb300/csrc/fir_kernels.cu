@@ -643,11 +643,18 @@ static void fir_opt_in() {
     done[dev] = true;
 }
 
-void prepare_fir_launches() { fir_opt_in(); }
+void prepare_fir_launches() {
+    fir_opt_in();
+    prepare_fused_launches();
+}
 
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s, const FirTma* tma) {
     if (ctas <= 0) return;
+    if (variant == kFirFused) {  // both passes in the pass-0 launch
+        if (pass == 0) launch_fir_fused(grids, map, ctas, D, s);
+        return;
+    }
     fir_opt_in();
     if (variant == kFirLargeRadius && map == nullptr && tma && tma->ok) {
         // persistent: at most one CTA per SM walks the tiles

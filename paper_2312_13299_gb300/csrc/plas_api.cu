@@ -358,6 +358,7 @@ int plas_set_tuning(int H, int W, int D, const plas_tuning* t) {
     tu.medium_below = t->fir_medium_below;
     tu.assign_per_sm = t->assign_ctas_per_sm;
     tu.large_tma = t->large_tma ? 1 : 0;
+    tu.small_fused = t->small_fused ? 1 : 0;
     install_tuning(H, W, D, &tu);
     return PLAS_OK;
 }
@@ -372,6 +373,7 @@ int plas_get_tuning(int H, int W, int D, plas_tuning* out) {
     out->fir_medium_below = t.medium_below;
     out->assign_ctas_per_sm = t.assign_per_sm;
     out->large_tma = t.large_tma;
+    out->small_fused = t.small_fused;
     return PLAS_OK;
 }
 
@@ -505,11 +507,11 @@ static int target_impl(const float* x, int H, int W, int D, const float* weights
             launch_box_target(ws.ref, H, W, D, num_sms(), st);
         } else {
             const Tuning tu = tuning_for(H, W, D);
-            const int var = fir_tiling(g.lv[0].r, tu);
+            const int var = fir_variant(g.lv[0].r, D, tu);
             FirTma tma;
             if (tu.large_tma) make_fir_tma(ws.G, ws.H1, H, W, D, g.max_steps, &tma);
-            launch_fir(0, ws.ref, nullptr, fir_ctas(H, W * D, var), D, var, st, &tma);
-            launch_fir(1, ws.ref, nullptr, fir_ctas(W, H * D, var), D, var, st, &tma);
+            launch_fir(0, ws.ref, nullptr, fir_pass_ctas(0, H, W, D, var), D, var, st, &tma);
+            launch_fir(1, ws.ref, nullptr, fir_pass_ctas(1, H, W, D, var), D, var, st, &tma);
         }
         launch_copy_features(ws.T, (int)N, D, target_stride(D), T, st);
         rc = check_launch("target");

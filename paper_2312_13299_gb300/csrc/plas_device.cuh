@@ -119,6 +119,9 @@ struct DevState {
     double fmas_y;            // in-range tap FMAs of the passes along y
     double fmas_x;            // in-range tap FMAs of the passes along x
     double beta2_sum;         // grouping-table entries generated
+    int fused_pending;        // the running iteration's target ran both passes in one launch
+    long long fused_its;      // iterations whose target ran in one launch
+    double fmas_xf;           // the pass-along-x FMAs of those iterations (not in fmas_x)
     unsigned int lo_bits[64]; // per-channel minimum, order-preserving encoding
     unsigned int hi_bits[64]; // per-channel maximum, order-preserving encoding
 };

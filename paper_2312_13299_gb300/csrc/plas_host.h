@@ -96,9 +96,17 @@ struct Tuning {
     int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row
     int assign_per_sm = kDefaultAssignPerSm;
     int large_tma = 1;  // the large tiling streams rows with tensor copies where a grid allows
+    int small_fused = 1;  // small radii run both passes in one launch where eligible
 };
 inline int fir_tiling(int r, const Tuning& t) {
     return r < t.small_below ? kFirSmallRadius : r < t.medium_below ? kFirMediumRadius : kFirLargeRadius;
+}
+// The FIR variant a level of radius r runs for D channels: the small-radius
+// path takes the one-launch kernel up to kFusedMaxR and 16 channels (radii
+// only shrink within a sort, so a plan made at radius r stays eligible).
+inline int fir_variant(int r, int D, const Tuning& t) {
+    const int v = fir_tiling(r, t);
+    return v == kFirSmallRadius && t.small_fused && D <= kFusedMaxD && r <= kFusedMaxR ? kFirFused : v;
 }
 Tuning tuning_for(int H, int W, int D);
 void install_tuning(int H, int W, int D, const Tuning* t);  // nullptr removes

@@ -386,7 +386,13 @@ static __device__ void schedule_step(DevState* st, long long N, int nby, int nbx
                               int nlevels, double tol, long long* trace_S, int* trace_level,
                               long long trace_cap, double fmas_y, double fmas_x, double beta2) {
     st->fmas_y += fmas_y;
-    st->fmas_x += fmas_x;
+    if (st->fused_pending) {  // both passes ran in the pass-0 launch
+        st->fmas_xf += fmas_x;
+        st->fused_its += 1;
+        st->fused_pending = 0;
+    } else {
+        st->fmas_x += fmas_x;
+    }
     st->beta2_sum += beta2;
     const unsigned long long S = atomicAdd(&st->S, 0ull);
     const double denom = ldexp((double)N, st->scale_exp);

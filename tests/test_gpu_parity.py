@@ -76,9 +76,11 @@ def test_target_bitexact_wide_magnitudes(plas, orc, phi):
 
 
 # tuning that forces one FIR tiling at every radius: (small_below,
-# medium_below, large_tma)
-_TILINGS = {"direct": (10 ** 6, 10 ** 6, 0), "64-row": (0, 10 ** 6, 0), "128-row": (0, 0, 0),
-            "128-row-tensor-copy": (0, 0, 1)}
+# medium_below, large_tma, small_fused); "one-launch" runs both passes in one
+# kernel up to r = 11 and the direct kernel above
+_TILINGS = {"direct": (10 ** 6, 10 ** 6, 0, 0), "one-launch": (10 ** 6, 10 ** 6, 0, 1),
+            "64-row": (0, 10 ** 6, 0, 1), "128-row": (0, 0, 0, 1),
+            "128-row-tensor-copy": (0, 0, 1, 1)}
 
 
 @pytest.mark.parametrize("tiling", sorted(_TILINGS))
@@ -96,9 +98,33 @@ def test_target_bitexact_every_tiling(plas, orc, tiling, H, W, D, phi):
     rng = np.random.default_rng(H * 7 + W * 3 + D)
     x = rng.random((H * W, D), dtype=np.float32)
     perm = rng.permutation(H * W).astype(np.int32)
-    sb, mb, tma = _TILINGS[tiling]
+    sb, mb, tma, fused = _TILINGS[tiling]
     plas.set_tuning(H, W, D, fir_small_below=sb, fir_medium_below=mb, assign_ctas_per_sm=8,
-                    large_tma=tma)
+                    large_tma=tma, small_fused=fused)
+    try:
+        got = plas.target(_cuda(x), H, W, _cuda(perm), phi).cpu().numpy()
+    finally:
+        plas.set_tuning(H, W, D)
+    want = orc.target(x, H, W, perm, phi)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("H,W,D,phi", [(200, 136, 14, 1.0), (200, 136, 14, 5.5), (131, 77, 5, 2.0),
+                                       (131, 77, 5, 11.9), (96, 160, 3, 3.0), (96, 160, 3, 8.0),
+                                       (1, 300, 14, 7.0), (257, 1, 2, 9.0), (33, 70, 16, 11.0),
+                                       (50, 40, 1, 4.0), (45, 38, 15, 10.0), (64, 64, 4, 6.0),
+                                       (7, 9, 13, 3.0), (40, 31, 7, 11.0), (12, 5, 11, 2.0)])
+def test_target_bitexact_small_radii(plas, orc, fused, H, W, D, phi):
+    """Radii 1-11 on the small-radius path: both passes in one launch (tiles
+    of 32 x 32 cells with the pass along y kept in shared memory; halos cut by
+    the border; odd D, where the last channel pair carries the index column)
+    and the two-launch direct kernel give the oracle's target bit for bit,
+    also on grids narrower than the halo and single rows or columns."""
+    rng = np.random.default_rng(H * 5 + W * 11 + D + int(phi))
+    x = rng.random((H * W, D), dtype=np.float32)
+    perm = rng.permutation(H * W).astype(np.int32)
+    plas.set_tuning(H, W, D, fir_small_below=10 ** 6, fir_medium_below=10 ** 6, small_fused=fused)
     try:
         got = plas.target(_cuda(x), H, W, _cuda(perm), phi).cpu().numpy()
     finally:
@@ -234,13 +260,12 @@ def test_autotune_and_forced_launch_shapes_give_identical_results(plas, orc):
     want = orc.sort(x, H, W, seed=11)
     xc = _cuda(x)
     try:
-        for small_below, medium_below, per_sm, tma in [(0, 0, 1, 0), (0, 0, 2, 1),
-                                                       (10 ** 6, 10 ** 6, 16, 1), (0, 10 ** 6, 2, 0),
-                                                       (3, 12, 8, 1),
-                                                       (t["fir_small_below"], t["fir_medium_below"], 4,
-                                                        t["large_tma"])]:
+        for small_below, medium_below, per_sm, tma, fused in [
+                (0, 0, 1, 0, 1), (0, 0, 2, 1, 1), (10 ** 6, 10 ** 6, 16, 1, 1),
+                (10 ** 6, 10 ** 6, 16, 1, 0), (0, 10 ** 6, 2, 0, 1), (3, 12, 8, 1, 1),
+                (t["fir_small_below"], t["fir_medium_below"], 4, t["large_tma"], t["small_fused"])]:
             plas.set_tuning(H, W, D, fir_small_below=small_below, fir_medium_below=medium_below,
-                            assign_ctas_per_sm=per_sm, large_tma=tma)
+                            assign_ctas_per_sm=per_sm, large_tma=tma, small_fused=fused)
             got = plas.sort(xc, H, W, seed=11, trace_cap=1 << 14)
             assert np.array_equal(got.perm.cpu().numpy(), want["perm"]), (small_below, medium_below,
                                                                           per_sm)
