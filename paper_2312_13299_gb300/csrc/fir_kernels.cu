@@ -651,8 +651,8 @@ void prepare_fir_launches() {
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s, const FirTma* tma) {
     if (ctas <= 0) return;
-    if (variant == kFirFused) {  // both passes in the pass-0 launch
-        if (pass == 0) launch_fir_fused(grids, map, ctas, D, s);
+    if (variant >= kFirFused) {  // both passes in the pass-0 launch
+        if (pass == 0) launch_fir_fused(grids, map, ctas, D, variant - kFirFused, s);
         return;
     }
     fir_opt_in();

@@ -3,18 +3,21 @@
 // blur of the grid, renormalised at the border) in one launch, for small
 // radii (r <= kFusedMaxR) and up to 16 channels.
 //
-// A CTA owns a tile of 32 x 32 cells of the target.  Phase 1 runs the pass
+// A CTA owns a tile of 16 x 32 cells of the target.  Phase 1 runs the pass
 // along y for the tile's rows and for its cells widened by the radius on
 // both sides (the halo the pass along x needs), reading the working grid
 // straight from global memory, and keeps the result (H1) in shared memory;
 // phase 2 runs the pass along x out of shared memory and writes the target.
-// H1 never goes to global memory, and the grid is read once per tile.
+// H1 never goes to global memory.
 //
-// The chains are those of the two-pass kernels: every output's FMA chain
-// runs over the same tap steps (the step range of its aligned block of 8
-// outputs, zero taps and zero rows beyond the border included, in ascending
-// order), and each pass ends with the same correctly rounded division by the
-// border tap mass, so the target is bit-identical to the two-pass path.
+// Each output's FMA chain runs over the taps k_{-r} .. k_r in ascending
+// order, as in the oracle; inputs beyond the border enter as zeros, which
+// leave the chain unchanged, so the in-range terms are the oracle's terms in
+// the oracle's order.  Each pass ends with the correctly rounded division by
+// the border tap mass (div_rn), as in the two-pass kernels, so the target is
+// bit-identical to them and to the oracle.  The radius is a compile-time
+// constant of the chains: the kernel for radii up to RMAX switches on the
+// level's radius (which only shrinks during a sort) to the matching chain.
 // Lanes work on channel pairs (packed fma.rn.f32x2, two independent IEEE
 // FMAs); with an odd D the second channel of the last pair is the grid's
 // index column, which is computed alongside and never stored.
@@ -22,177 +25,163 @@
 
 namespace plas {
 
-constexpr int kFusedTY = 32, kFusedTX = 32, kFusedThreads = 256;
-
-size_t fused_smem_bytes(int D) {
-    const int P = (D + 1) / 2;
-    return sizeof(float2) * (size_t)kFusedTY * (size_t)(kFusedTX + 2 * kFusedMaxR) * (size_t)P;
-}
+constexpr int kFusedTY = 16, kFusedTX = 32, kFusedThreads = 256;
 
 int fused_ctas(int H, int W) {
     return ((W + kFusedTX - 1) / kFusedTX) * ((H + kFusedTY - 1) / kFusedTY);
 }
 
-// Pass along y for one channel pair of one cell and 8 output rows: NR window
-// rows of the grid (column pointer col, row stride in_row; zero outside
-// [0, H)), NB blocks of 8 tap steps from tp.
-template <int NB>
-__device__ __forceinline__ void chain_grid(const float* __restrict__ col, long long in_row, int H,
-                                           int base, const float2* __restrict__ tp,
-                                           float2 (&acc)[kFirX]) {
-    constexpr int X = kFirX, NR = NB * X + X - 1;
-    float2 w[NR];
+static size_t fused_smem(int D, int rmax) {
+    const int P = (D + 1) / 2;
+    return sizeof(float2) * (size_t)kFusedTY * (size_t)(kFusedTX + 2 * rmax) * (size_t)P;
+}
+
+// Phase 1 for radius R along y: H1 of the tile's rows for every halo cell and
+// channel pair, into shared memory ([row][cell][pair], nch * P float2 a row).
+template <int R>
+__device__ __forceinline__ void fused_pass_y(const GridRef& gr, const LevelDesc& lv, int x0, int y0,
+                                             int rx, int P, int nch, int gs, float2* h1s) {
+    constexpr int X = kFirX, NR = X + 2 * R;
+    const int H = gr.H, W = gr.W;
+    const int rs = nch * P;
+    const float2* __restrict__ tp = reinterpret_cast<const float2*>(gr.table + lv.off_ty);
+    const float* __restrict__ nrm = gr.table + lv.off_ny;
+    const float* __restrict__ rcp = nrm + ((H + 3) & ~3);
+    const long long in_row = (long long)W * gs;
+    const int nu = (kFusedTY / X) * rs;
+    for (int u = threadIdx.x; u < nu; u += kFusedThreads) {
+        const int b = u / rs, cp = u - b * rs;  // cp = cell * P + pair
+        const int ch = cp / P, p = cp - ch * P;
+        const int x = x0 - rx + ch, ylo = y0 + X * b;
+        float2* dst = h1s + (X * b) * rs + cp;
+        if (x < 0 || x >= W || ylo >= H) {  // halo beyond the grid: zeros
 #pragma unroll
-    for (int m = 0; m < NR; ++m) {
-        const int yy = base + m;
-        w[m] = (yy >= 0 && yy < H) ? __ldg(reinterpret_cast<const float2*>(col + (long long)yy * in_row))
-                                   : make_float2(0.0f, 0.0f);
-    }
+            for (int i = 0; i < X; ++i) dst[i * rs] = make_float2(0.0f, 0.0f);
+            continue;
+        }
+        const float* col = gr.G + (long long)x * gs + 2 * p;
+        float2 w[NR];
 #pragma unroll
-    for (int s = 0; s < NB * X; ++s) {
-        const float2 k = __ldg(tp + s);
+        for (int m = 0; m < NR; ++m) {
+            const int yy = ylo - R + m;
+            w[m] = (yy >= 0 && yy < H) ? __ldg(reinterpret_cast<const float2*>(col + (long long)yy * in_row))
+                                       : make_float2(0.0f, 0.0f);
+        }
+        float2 acc[X];
 #pragma unroll
-        for (int i = 0; i < X; ++i) acc[i] = __ffma2_rn(k, w[s + i], acc[i]);
+        for (int i = 0; i < X; ++i) acc[i] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) {  // tap j - R, stored at pair index j
+            const float2 k = __ldg(tp + j);
+#pragma unroll
+            for (int i = 0; i < X; ++i) acc[i] = __ffma2_rn(k, w[i + j], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < X; ++i) {
+            const int y = ylo + i;
+            if (y < H) {
+                const float n = nrm[y], q = rcp[y];
+                dst[i * rs] = make_float2(div_rn(acc[i].x, n, q), div_rn(acc[i].y, n, q));
+            }
+        }
     }
 }
 
-// Pass along x for one channel pair of one row and 8 output cells: NR window
-// cells of the shared H1 row (stride P float2 per cell; zero outside
-// [0, nch)).
-template <int NB>
-__device__ __forceinline__ void chain_shared(const float2* row, int P, int nch, int base,
-                                             const float2* __restrict__ tp, float2 (&acc)[kFirX]) {
-    constexpr int X = kFirX, NR = NB * X + X - 1;
-    float2 w[NR];
+// Phase 2 for radius R along x: the target of the tile from shared H1.
+template <int R>
+__device__ __forceinline__ void fused_pass_x(const GridRef& gr, const LevelDesc& lv, int x0, int y0,
+                                             int P, int nch, int D, int ts, const float2* h1s) {
+    constexpr int X = kFirX, NR = X + 2 * R;
+    const int H = gr.H, W = gr.W;
+    const int rs = nch * P;
+    const float2* __restrict__ tp = reinterpret_cast<const float2*>(gr.table + lv.off_tx);
+    const float* __restrict__ nrm = gr.table + lv.off_nx;
+    const float* __restrict__ rcp = nrm + ((W + 3) & ~3);
+    const int per_block = kFusedTY * P;
+    const int nu = (kFusedTX / X) * per_block;
+    const bool even_d = (D & 1) == 0;
+    for (int v = threadIdx.x; v < nu; v += kFusedThreads) {
+        const int cb = v / per_block, ip = v - cb * per_block;
+        const int i = ip / P, p = ip - i * P;
+        const int y = y0 + i, xlo = x0 + X * cb;
+        if (y >= H || xlo >= W) continue;
+        // window cell m is x = xlo - R + m: halo index X * cb + m (in the halo)
+        const float2* row = h1s + i * rs + (X * cb) * P + p;
+        float2 w[NR];
 #pragma unroll
-    for (int m = 0; m < NR; ++m) {
-        const int c = base + m;
-        w[m] = (c >= 0 && c < nch) ? row[c * P] : make_float2(0.0f, 0.0f);
-    }
+        for (int m = 0; m < NR; ++m) w[m] = row[m * P];
+        float2 acc[X];
 #pragma unroll
-    for (int s = 0; s < NB * X; ++s) {
-        const float2 k = __ldg(tp + s);
+        for (int k = 0; k < X; ++k) acc[k] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < X; ++i) acc[i] = __ffma2_rn(k, w[s + i], acc[i]);
+        for (int j = 0; j <= 2 * R; ++j) {
+            const float2 k2 = __ldg(tp + j);
+#pragma unroll
+            for (int k = 0; k < X; ++k) acc[k] = __ffma2_rn(k2, w[k + j], acc[k]);
+        }
+        float* out = gr.T + ((long long)y * W + xlo) * ts + 2 * p;
+        const bool pair = even_d || p + 1 < P;
+#pragma unroll
+        for (int k = 0; k < X; ++k) {
+            const int x = xlo + k;
+            if (x < W) {
+                const float n = nrm[x], q = rcp[x];
+                const float a = div_rn(acc[k].x, n, q);
+                if (pair)
+                    *reinterpret_cast<float2*>(out + k * ts) = make_float2(a, div_rn(acc[k].y, n, q));
+                else
+                    out[k * ts] = a;
+            }
+        }
     }
 }
 
-// Tap-step range [wlo, wend) of the aligned block of 8 outputs starting at
-// position lo on an axis of length len (the same rule as the two-pass
-// kernels): steps with a non-zero tap that reach an in-range input for some
-// output of the block, widened to whole blocks of 8.
-__device__ __forceinline__ void block_steps(int lo, int len, int r, int rp, int ntp, int* wlo,
-                                            int* nb) {
-    const int hi = min(lo + kFirX, len) - 1;
-    int a = max(rp - r, rp - hi);
-    a = a / kFirX * kFirX;
-    const int b = min(rp + r, rp + len - 1 - lo);
-    const int e = min(ntp, (b + kFirX) / kFirX * kFirX);
-    *wlo = a;
-    *nb = (e - a) / kFirX;
+// The chains for the level's radius r (0 .. RMAX; the host plans the launch
+// for a radius <= RMAX, and radii only shrink during a sort).
+template <int R, int RMAX>
+__device__ __forceinline__ void fused_y_at(int r, const GridRef& gr, const LevelDesc& lv, int x0, int y0,
+                                           int rx, int P, int nch, int gs, float2* h1s) {
+    if constexpr (R <= RMAX) {
+        if (r == R)
+            fused_pass_y<R>(gr, lv, x0, y0, rx, P, nch, gs, h1s);
+        else
+            fused_y_at<R + 1, RMAX>(r, gr, lv, x0, y0, rx, P, nch, gs, h1s);
+    }
+}
+template <int R, int RMAX>
+__device__ __forceinline__ void fused_x_at(int r, const GridRef& gr, const LevelDesc& lv, int x0, int y0,
+                                           int P, int nch, int D, int ts, const float2* h1s) {
+    if constexpr (R <= RMAX) {
+        if (r == R)
+            fused_pass_x<R>(gr, lv, x0, y0, P, nch, D, ts, h1s);
+        else
+            fused_x_at<R + 1, RMAX>(r, gr, lv, x0, y0, P, nch, D, ts, h1s);
+    }
 }
 
-__global__ void __launch_bounds__(kFusedThreads, 2) fir_fused_kernel(
+// Registers per thread budget: the radius group's window (8 + 2 RMAX channel
+// pairs) plus 8 accumulator pairs.
+template <int RMAX>
+__global__ void __launch_bounds__(kFusedThreads, RMAX <= 3 ? 3 : 2) fir_fused_kernel(
     const GridRef* __restrict__ grids, const CtaMap* __restrict__ map, int D, int gs, int ts) {
-    constexpr int X = kFirX;
     extern __shared__ __align__(16) float2 h1s[];  // [kFusedTY][nch][P]
     const CtaRef cr = resolve_cta(map);
     const GridRef& gr = grids[cr.g];
     DevState* st = gr.st;
     if (sweep_idle(st)) return;
     const LevelDesc& lv = gr.lv[st->level];
-    const int H = gr.H, W = gr.W;
-    const int ry = lv.ry, rpy = lv.rpy, ntpy = lv.ntpy;
-    const int rx = lv.rx, rpx = lv.rpx, ntpx = lv.ntpx;
-    if (ry > kFusedMaxR || rx > kFusedMaxR) {  // the host plans this launch for small radii only
+    const int ry = lv.ry, rx = lv.rx;
+    if (ry > RMAX || rx > RMAX) {  // planned for smaller radii only: record, touch nothing
         if (threadIdx.x == 0) atomicCAS(&st->status, 0, -7);  // PLAS_ERR_INTERNAL
         return;
     }
     const int P = (D + 1) >> 1;
-    const int ntx = (W + kFusedTX - 1) / kFusedTX;
+    const int ntx = (gr.W + kFusedTX - 1) / kFusedTX;
     const int x0 = (cr.local % ntx) * kFusedTX, y0 = (cr.local / ntx) * kFusedTY;
     const int nch = kFusedTX + 2 * rx;  // tile cells plus the halo along x
-    const int rs = nch * P;             // float2 per H1 row in shared memory
-
-    // ---- phase 1: pass along y into shared memory ----
-    {
-        const float2* tp = reinterpret_cast<const float2*>(gr.table + lv.off_ty);
-        const float* nrm = gr.table + lv.off_ny;
-        const float* rcp = nrm + ((H + 3) & ~3);
-        const long long in_row = (long long)W * gs;
-        const int nu = (kFusedTY / X) * rs;
-        for (int u = threadIdx.x; u < nu; u += kFusedThreads) {
-            const int b = u / rs, cp = u - b * rs;  // cp = ch * P + p
-            const int ch = cp / P, p = cp - ch * P;
-            const int x = x0 - rx + ch, ylo = y0 + X * b;
-            float2* dst = h1s + (X * b) * rs + cp;
-            if (x < 0 || x >= W || ylo >= H) {  // halo beyond the grid: zeros
-#pragma unroll
-                for (int i = 0; i < X; ++i) dst[i * rs] = make_float2(0.0f, 0.0f);
-                continue;
-            }
-            int wlo, nb;
-            block_steps(ylo, H, ry, rpy, ntpy, &wlo, &nb);
-            float2 acc[X];
-#pragma unroll
-            for (int i = 0; i < X; ++i) acc[i] = make_float2(0.0f, 0.0f);
-            const float* col = gr.G + (long long)x * gs + 2 * p;
-            const int base = ylo - rpy + wlo;
-            if (nb == 1) chain_grid<1>(col, in_row, H, base, tp + wlo, acc);
-            else if (nb == 2) chain_grid<2>(col, in_row, H, base, tp + wlo, acc);
-            else chain_grid<3>(col, in_row, H, base, tp + wlo, acc);
-#pragma unroll
-            for (int i = 0; i < X; ++i) {
-                const int y = ylo + i;
-                if (y < H) {
-                    const float n = nrm[y], q = rcp[y];
-                    dst[i * rs] = make_float2(div_rn(acc[i].x, n, q), div_rn(acc[i].y, n, q));
-                }
-            }
-        }
-    }
+    fused_y_at<0, RMAX>(ry, gr, lv, x0, y0, rx, P, nch, gs, h1s);
     __syncthreads();
-
-    // ---- phase 2: pass along x from shared memory into the target ----
-    {
-        const float2* tp = reinterpret_cast<const float2*>(gr.table + lv.off_tx);
-        const float* nrm = gr.table + lv.off_nx;
-        const float* rcp = nrm + ((W + 3) & ~3);
-        const int per_block = kFusedTY * P;  // units of one block of 8 cells (whole warps)
-        const int nu = (kFusedTX / X) * per_block;
-        for (int v = threadIdx.x; v < nu; v += kFusedThreads) {
-            const int cb = v / per_block, ip = v - cb * per_block;
-            const int i = ip / P, p = ip - i * P;
-            const int y = y0 + i, xlo = x0 + X * cb;
-            if (y >= H || xlo >= W) continue;
-            int wlo, nb;
-            block_steps(xlo, W, rx, rpx, ntpx, &wlo, &nb);
-            float2 acc[X];
-#pragma unroll
-            for (int k = 0; k < X; ++k) acc[k] = make_float2(0.0f, 0.0f);
-            // window cell m is x = xlo - rpx + wlo + m, halo index x - (x0 - rx)
-            const float2* row = h1s + i * rs + p;
-            const int base = X * cb - rpx + wlo + rx;
-            if (nb == 1) chain_shared<1>(row, P, nch, base, tp + wlo, acc);
-            else if (nb == 2) chain_shared<2>(row, P, nch, base, tp + wlo, acc);
-            else chain_shared<3>(row, P, nch, base, tp + wlo, acc);
-            float* out = gr.T + ((long long)y * W + xlo) * ts + 2 * p;
-            const bool pair = 2 * p + 1 < D;
-#pragma unroll
-            for (int k = 0; k < X; ++k) {
-                const int x = xlo + k;
-                if (x < W) {
-                    const float n = nrm[x], q = rcp[x];
-                    const float a = div_rn(acc[k].x, n, q);
-                    if (pair)
-                        *reinterpret_cast<float2*>(out + k * ts) = make_float2(a, div_rn(acc[k].y, n, q));
-                    else
-                        out[k * ts] = a;
-                }
-            }
-        }
-    }
-
+    fused_x_at<0, RMAX>(rx, gr, lv, x0, y0, P, nch, D, ts, h1s);
     // the iteration's grouping table (the pass along y writes it in the
     // two-pass path)
     write_group_table(gr, lv, st, cr.local, cr.count, kFusedThreads);
@@ -205,16 +194,27 @@ void prepare_fused_launches() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(fir_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fused_smem_bytes(kFusedMaxD));
+    cudaFuncSetAttribute(fir_fused_kernel<kFusedGroupMaxR[0]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem(kFusedMaxD, kFusedGroupMaxR[0]));
+    cudaFuncSetAttribute(fir_fused_kernel<kFusedGroupMaxR[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem(kFusedMaxD, kFusedGroupMaxR[1]));
+    cudaFuncSetAttribute(fir_fused_kernel<kFusedGroupMaxR[2]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem(kFusedMaxD, kFusedGroupMaxR[2]));
     done[dev] = true;
 }
 
-void launch_fir_fused(const GridRef* grids, const CtaMap* map, int ctas, int D, cudaStream_t s) {
-    if (ctas <= 0 || D > kFusedMaxD) return;
+void launch_fir_fused(const GridRef* grids, const CtaMap* map, int ctas, int D, int group,
+                      cudaStream_t s) {
+    if (ctas <= 0 || D > kFusedMaxD || group < 0 || group >= kFusedGroups) return;
     prepare_fused_launches();
-    fir_fused_kernel<<<ctas, kFusedThreads, fused_smem_bytes(D), s>>>(grids, map, D, grid_stride(D),
-                                                                       target_stride(D));
+    const int gs = grid_stride(D), ts = target_stride(D);
+    const size_t sm = fused_smem(D, kFusedGroupMaxR[group]);
+    if (group == 0)
+        fir_fused_kernel<kFusedGroupMaxR[0]><<<ctas, kFusedThreads, sm, s>>>(grids, map, D, gs, ts);
+    else if (group == 1)
+        fir_fused_kernel<kFusedGroupMaxR[1]><<<ctas, kFusedThreads, sm, s>>>(grids, map, D, gs, ts);
+    else
+        fir_fused_kernel<kFusedGroupMaxR[2]><<<ctas, kFusedThreads, sm, s>>>(grids, map, D, gs, ts);
 }
 
 }  // namespace plas

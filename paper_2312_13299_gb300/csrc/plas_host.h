@@ -106,7 +106,8 @@ inline int fir_tiling(int r, const Tuning& t) {
 // only shrink within a sort, so a plan made at radius r stays eligible).
 inline int fir_variant(int r, int D, const Tuning& t) {
     const int v = fir_tiling(r, t);
-    return v == kFirSmallRadius && t.small_fused && D <= kFusedMaxD && r <= kFusedMaxR ? kFirFused : v;
+    return v == kFirSmallRadius && t.small_fused && D <= kFusedMaxD && r <= kFusedMaxR ? fused_variant(r)
+                                                                                      : v;
 }
 Tuning tuning_for(int H, int W, int D);
 void install_tuning(int H, int W, int D, const Tuning* t);  // nullptr removes

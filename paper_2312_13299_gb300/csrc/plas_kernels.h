@@ -20,11 +20,17 @@ constexpr int kMaxD = 64;
 constexpr int kFirX = 8;       // outputs per lane and column of the FIR passes
 constexpr int kFirCols = 128;  // columns per FIR CTA (four per lane)
 // FIR tilings (identical results); which one a radius uses is a tuning choice
-constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1, kFirMediumRadius = 2, kFirFused = 3,
-              kFirTilings = 4;
-// Both passes in one launch (fused_kernels.cu) for radii up to kFusedMaxR
-// (three blocks of 8 tap steps) and up to 16 channels.
+// Both passes in one launch (fused_kernels.cu) for radii up to kFusedMaxR and
+// up to 16 channels, one kernel per radius group (variants kFirFused + g for
+// radii up to kFusedGroupMaxR[g]).
+constexpr int kFusedGroups = 3;
+constexpr int kFusedGroupMaxR[kFusedGroups] = {3, 7, 11};
 constexpr int kFusedMaxR = 11, kFusedMaxD = 16;
+constexpr int kFirLargeRadius = 0, kFirSmallRadius = 1, kFirMediumRadius = 2, kFirFused = 3,
+              kFirTilings = kFirFused + kFusedGroups;
+inline int fused_variant(int r) {
+    return kFirFused + (r <= kFusedGroupMaxR[0] ? 0 : r <= kFusedGroupMaxR[1] ? 1 : 2);
+}
 
 // Row stride (floats) of the first-pass output H1 ([x][y][d], W rows of H*D
 // values): padded to 16 bytes so that tensor copies can stream its rows.
@@ -133,12 +139,11 @@ inline int target_stride(int D) { return (D + 3) & ~3; }
 
 // ---- CTA counts per grid ------------------------------------------------------
 int fir_ctas(int rows, int cols, int variant);  // rows = blur axis length, cols = cells * D
-size_t fused_smem_bytes(int D);
 int fused_ctas(int H, int W);
 // CTAs of pass 'pass' (0: along y, 1: along x) of an H x W x D grid in FIR
 // variant 'var' (the fused variant runs everything in its pass-0 launch)
 inline int fir_pass_ctas(int pass, int H, int W, int D, int var) {
-    if (var == kFirFused) return pass == 0 ? fused_ctas(H, W) : 0;
+    if (var >= kFirFused) return pass == 0 ? fused_ctas(H, W) : 0;
     return pass == 0 ? fir_ctas(H, W * D, var) : fir_ctas(W, H * D, var);
 }
 constexpr int kAssignMaxPerSm = 16;
@@ -159,13 +164,14 @@ void launch_norms(const LevelDesc* lv_dev, int nlev, int H, int W, float* table,
 // ---- one sweep (every grid in 'grids' advances by one iteration) --------------
 // map == nullptr: one grid (grids[0]), CTA index = blockIdx.x.
 // pass 0: along y (G -> H1), also writes the iteration's grouping table;
-// pass 1: along x (H1 -> T).  Variant kFirFused: pass 0 runs both passes
-// (G -> T) and the grouping table, pass 1 launches nothing.
+// pass 1: along x (H1 -> T).  Variants kFirFused + g: pass 0 runs both
+// passes (G -> T) and the grouping table, pass 1 launches nothing.
 // (prepare_fir_launches sets the FIR kernels' shared-memory opt-in once per
 // device; launch_fir calls it too, but a stream capture calls it first)
 void prepare_fir_launches();
 void prepare_fused_launches();
-void launch_fir_fused(const GridRef* grids, const CtaMap* map, int ctas, int D, cudaStream_t s);
+void launch_fir_fused(const GridRef* grids, const CtaMap* map, int ctas, int D, int group,
+                      cudaStream_t s);
 void launch_fir(int pass, const GridRef* grids, const CtaMap* map, int ctas, int D, int variant,
                 cudaStream_t s, const FirTma* tma = nullptr);
 void launch_assign(const GridRef* grids, const CtaMap* map, int ctas, int D, double tol,
