@@ -51,10 +51,15 @@ def test_tuning_table_round_trip_host_only():
     """The launch-shape table is host state: install, look up (nearest cell
     count for the same D), validate and remove -- no device work."""
     import paper_2312_13299_gb300 as plas
+    assert plas.get_tuning(64, 64, 5)["small_fused"] == 1   # both passes in one launch by default
     plas.set_tuning(64, 64, 5, fir_small_below=7, fir_medium_below=40, assign_ctas_per_sm=3)
     try:
         t = plas.get_tuning(64, 64, 5)
         assert (t["fir_small_below"], t["fir_medium_below"], t["assign_ctas_per_sm"]) == (7, 40, 3)
+        assert t["small_fused"] == 1
+        plas.set_tuning(64, 64, 5, small_fused=False)
+        assert plas.get_tuning(64, 64, 5)["small_fused"] == 0
+        assert plas.get_tuning(64, 64, 5)["fir_small_below"] == 7
         assert plas.get_tuning(70, 60, 5)["fir_small_below"] == 7   # nearest entry, same D
         d = plas.get_tuning(64, 64, 6)                              # other D: defaults
         assert (d["fir_small_below"], d["fir_medium_below"], d["assign_ctas_per_sm"]) == (
