@@ -56,7 +56,7 @@ FP32_FMA_LANES_PER_SM = 128  # sm_103a: 4 SM sub-partitions x 32 FP32 lanes
 # keyed by the sha1 of the target-pass sources it was taken on: a stale hash
 # reports null.
 NCU_TRAFFIC = {
-    ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 85932083, "src": "5b5501039845"},
+    ("blur_cols", "3dgs-1024"): {"bytes_per_launch": 94084815, "src": "8c506d80d500"},
 }
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
