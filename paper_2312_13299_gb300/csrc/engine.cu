@@ -55,7 +55,8 @@ struct Slot {
     long long N = 0;
     int nlev = 0;
     int ctas[kClsCount] = {0, 0, 0};
-    Tuning tune;  // FIR tiling choice (one-grid sweeps)
+    Tuning tune;  // FIR tiling choice
+    int fvar = kFirLargeRadius;  // FIR variant this grid's CTA maps hold (multi-grid sweeps)
     FirTma tma;   // the large tiling's tensor maps (one-grid sweeps)
     bool active = false;
     bool cancel = false;  // served request cancelled while admitted
@@ -84,11 +85,28 @@ struct SweepPlan {
     const GridRef* grids;
     const CtaMap* map[kClsCount];
     int ctas[kClsCount];
+    // multi-grid sweeps: one launch per FIR variant group and pass (the grids
+    // of a group share a variant; pass 1 of the one-launch variants is empty)
+    int nfg = 0;
+    int fvar[kFirTilings] = {};
+    int fctas[2][kFirTilings] = {};
+    const CtaMap* fmap[2][kFirTilings] = {};
     bool operator==(const SweepPlan& o) const {
-        if (k != o.k || var != o.var || grids != o.grids) return false;
+        if (k != o.k || var != o.var || grids != o.grids || nfg != o.nfg) return false;
         for (int c = 0; c < kClsCount; ++c)
             if (map[c] != o.map[c] || ctas[c] != o.ctas[c]) return false;
+        for (int g = 0; g < nfg; ++g)
+            if (fvar[g] != o.fvar[g] || fctas[0][g] != o.fctas[0][g] || fctas[1][g] != o.fctas[1][g] ||
+                fmap[0][g] != o.fmap[0][g] || fmap[1][g] != o.fmap[1][g])
+                return false;
         return true;
+    }
+    // kernel launches of one sweep
+    int launches() const {
+        int n = 1;  // assignment
+        if (nfg == 0) return n + (ctas[kClsFirY] > 0) + (ctas[kClsFirX] > 0);
+        for (int g = 0; g < nfg; ++g) n += (fctas[0][g] > 0) + (fctas[1][g] > 0);
+        return n;
     }
 };
 
@@ -213,8 +231,22 @@ class Engine {
     }
 
     // Enqueue k sweeps over the active grids.
+    // FIR variant of a grid at the radius it last reported
+    int grid_variant(const Slot* sl) const {
+        const int L = std::min(std::max(sl->last.level, 0), sl->nlev - 1);
+        return fir_variant(sl->geo.lv[L].r, D_, sl->tune);
+    }
+
     int sweeps(int k) {
         if (active_.empty()) return PLAS_OK;
+        if (!dirty_ && active_.size() > 1 && !want_persist()) {
+            // a grid whose radius now takes another FIR variant: new CTA maps
+            for (const Slot* sl : active_)
+                if (grid_variant(sl) != sl->fvar) {
+                    dirty_ = true;
+                    break;
+                }
+        }
         if (dirty_)
             if (int e = rebuild()) return e;
         SweepPlan p{};
@@ -228,6 +260,16 @@ class Engine {
         for (int c = 0; c < kClsCount; ++c) {
             p.map[c] = one ? nullptr : dmap_[c];
             p.ctas[c] = one ? active_[0]->ctas[c] : total_[c];
+        }
+        if (!one && !want_persist()) {
+            p.nfg = nfg_;
+            for (int g = 0; g < nfg_; ++g) {
+                p.fvar[g] = fvar_[g];
+                for (int pass = 0; pass < 2; ++pass) {
+                    p.fctas[pass][g] = fcnt_[pass][g];
+                    p.fmap[pass][g] = dmap_[pass == 0 ? kClsFirY : kClsFirX] + foff_[pass][g];
+                }
+            }
         }
         if (one) {
             const Slot* sl = active_[0];
@@ -256,7 +298,7 @@ class Engine {
             }
             return check_launch("persistent sweep");
         }
-        launches_ += (long long)k * kClsCount;
+        launches_ += (long long)k * (s_.target_mode == 1 ? kClsCount : p.launches());
         if (s_.graphs && !s_.profile && !graphs_failed_) {
             // every kernel reads its grid's level from device state, so a batch
             // captured once replays unchanged until the grid set, the tiling or
@@ -425,15 +467,19 @@ class Engine {
                 cudaEvent_t e0 = events ? begin() : nullptr;
                 switch (c) {
                     case kClsFirY:
-                        if (s_.target_mode == 1)  // box target (single grid): all of it here
-                            launch_box_target(p.grids, active_[0]->job.H, active_[0]->job.W, D_, nsm_, st);
-                        else
-                            launch_fir(0, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
+                    case kClsFirX: {
+                        const int pass = c == kClsFirY ? 0 : 1;
+                        if (s_.target_mode == 1) {  // box target (single grid): all of it here
+                            if (pass == 0)
+                                launch_box_target(p.grids, active_[0]->job.H, active_[0]->job.W, D_, nsm_, st);
+                        } else if (p.nfg == 0) {
+                            launch_fir(pass, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
+                        } else {  // one launch per variant group of the grids
+                            for (int g = 0; g < p.nfg; ++g)
+                                launch_fir(pass, p.grids, p.fmap[pass][g], p.fctas[pass][g], D_, p.fvar[g], st);
+                        }
                         break;
-                    case kClsFirX:
-                        if (s_.target_mode != 1)
-                            launch_fir(1, p.grids, p.map[c], p.ctas[c], D_, p.var, st, tma_of(p));
-                        break;
+                    }
                     default: launch_assign(p.grids, p.map[c], p.ctas[c], D_, s_.tol, st, s_.checked != 0); break;
                 }
                 if (events) end(e0, c);
@@ -521,20 +567,41 @@ class Engine {
             r.checked = s_.checked;
             r.edge_blocks = s_.whole_blocks ? 0 : 1;
         }
-        // the persistent sweep runs the medium FIR tiling, separate launches
-        // the large one
+        // the persistent sweep runs the medium FIR tiling for every grid;
+        // separate launches give each grid the variant its last reported
+        // radius takes, one launch per variant group and pass
         persist_ = want_persist();
-        const int fv = persist_ ? kFirMediumRadius : kFirLargeRadius;
+        for (Slot* sl : active_) sl->fvar = persist_ ? kFirMediumRadius : grid_variant(sl);
+        nfg_ = 0;
+        for (int v = 0; v < kFirTilings; ++v)
+            for (const Slot* sl : active_)
+                if (sl->fvar == v) {
+                    fvar_[nfg_++] = v;
+                    break;
+                }
         std::vector<CtaMap> maps;
         for (int c = 0; c < kClsCount; ++c) {
             total_[c] = 0;
-            for (size_t i = 0; i < active_.size(); ++i) {
-                const Job& j = active_[i]->job;
-                const int n = c == kClsFirY   ? fir_ctas(j.H, j.W * D_, fv)
-                              : c == kClsFirX ? fir_ctas(j.W, j.H * D_, fv)
-                                              : active_[i]->ctas[c];
-                for (int l = 0; l < n; ++l) maps.push_back(CtaMap{(int)i, l, n, 0});
-                total_[c] += n;
+            if (c == kClsAssign) {
+                for (size_t i = 0; i < active_.size(); ++i) {
+                    const int n = active_[i]->ctas[c];
+                    for (int l = 0; l < n; ++l) maps.push_back(CtaMap{(int)i, l, n, 0});
+                    total_[c] += n;
+                }
+                continue;
+            }
+            const int pass = c == kClsFirY ? 0 : 1;
+            for (int g = 0; g < nfg_; ++g) {
+                foff_[pass][g] = total_[c];
+                fcnt_[pass][g] = 0;
+                for (size_t i = 0; i < active_.size(); ++i) {
+                    if (active_[i]->fvar != fvar_[g]) continue;
+                    const Job& j = active_[i]->job;
+                    const int n = fir_pass_ctas(pass, j.H, j.W, D_, fvar_[g]);
+                    for (int l = 0; l < n; ++l) maps.push_back(CtaMap{(int)i, l, n, 0});
+                    fcnt_[pass][g] += n;
+                    total_[c] += n;
+                }
             }
         }
         const size_t need = map_bytes(refs.size(), maps.size());
@@ -588,6 +655,12 @@ class Engine {
     GridRef* dgrids_ = nullptr;
     CtaMap* dmap_[kClsCount] = {nullptr, nullptr, nullptr};
     int total_[kClsCount] = {0, 0, 0};
+    // FIR variant groups of the multi-grid CTA maps: variant, and per pass the
+    // offset into the class's maps and the CTA count
+    int nfg_ = 0;
+    int fvar_[kFirTilings] = {};
+    int foff_[2][kFirTilings] = {};
+    int fcnt_[2][kFirTilings] = {};
     bool persist_ = false;  // the next sweeps run as one persistent launch
     char* host_ = nullptr;
     size_t host_cap_ = 0;
@@ -1031,11 +1104,15 @@ static size_t batch_bytes(int n, const plas_job* jobs, int D, const plas_schedul
         if (per_job) (*per_job)[i] = b;
         total += b;
         grids += 1;
-        // CTA maps sized for the tiling with the most tiles (the medium one,
-        // which persistent sweeps run)
-        ctas += std::max(fir_ctas(H, W * D, kFirLargeRadius), fir_ctas(H, W * D, kFirMediumRadius)) +
-                std::max(fir_ctas(W, H * D, kFirLargeRadius), fir_ctas(W, H * D, kFirMediumRadius)) +
-                assign_ctas(H, W, nsm, kAssignMaxPerSm);
+        // CTA maps sized for the FIR variant with the most tiles (a grid's
+        // variant follows its radius)
+        for (int pass = 0; pass < 2; ++pass) {
+            int m = 0;
+            for (int v = 0; v < kFirTilings; ++v)
+                if (v < kFirFused || D <= kFusedMaxD) m = std::max(m, fir_pass_ctas(pass, H, W, D, v));
+            ctas += m;
+        }
+        ctas += assign_ctas(H, W, nsm, kAssignMaxPerSm);
     }
     if (maps_at) *maps_at = total;
     return total + Engine::map_bytes(grids, ctas);
