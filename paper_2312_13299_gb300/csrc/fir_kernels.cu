@@ -607,11 +607,10 @@ __global__ void __launch_bounds__(kDirThreads) fir_direct_kernel(
                 const float nrm = norm[y];
                 const float rcp = rnorm[y];
                 float* orow = out + (long long)y * out_row;
-                float v[2] = {acc[i].x, acc[i].y};
-                div_rn_warp<2>(v, nrm, rcp);  // ylo and y < R are the same for the whole warp
+                const float v[2] = {acc[i].x, acc[i].y};
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
-                    if (ok[k]) orow[ooff[k]] = v[k];
+                    if (ok[k]) orow[ooff[k]] = div_rn(v[k], nrm, rcp);
             }
         }
     }

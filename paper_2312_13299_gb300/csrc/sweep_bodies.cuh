@@ -44,38 +44,12 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 // correctly rounded quotient (Markstein's theorem, IBM J. Res. Dev. 34(1),
 // 1990) as long as nothing underflows or overflows.  Magnitudes outside
 // [2^-60, 2^60] (and zero, NaN, Inf) take the IEEE division itself.
-__device__ __forceinline__ bool div_fast_ok(float a) {
+__device__ __forceinline__ float div_rn(float a, float b, float y) {
     const float m = fabsf(a);
-    return m >= 0x1p-60f && m <= 0x1p60f;
-}
-__device__ __forceinline__ float div_fast(float a, float b, float y) {
+    if (!(m >= 0x1p-60f && m <= 0x1p60f)) return __fdiv_rn(a, b);
     const float q = __fmul_rn(a, y);
     const float r = __fmaf_rn(-q, b, a);
     return __fmaf_rn(r, y, q);
-}
-__device__ __forceinline__ float div_rn(float a, float b, float y) {
-    return div_fast_ok(a) ? div_fast(a, b, y) : __fdiv_rn(a, b);
-}
-// div_rn of N values sharing the divisor, for a whole warp: the fast path for
-// every value, then, only if some lane of the warp holds a value outside the
-// fast path's range (one vote), the IEEE division for those values; so the
-// usual case issues no division code.  Same results as div_rn.
-template <int N>
-__device__ __forceinline__ void div_rn_warp(float (&v)[N], float b, float y) {
-    bool slow = false;
-    float q[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        slow = slow || !div_fast_ok(v[k]);
-        q[k] = div_fast(v[k], b, y);
-    }
-    if (__any_sync(0xFFFFFFFFu, slow)) {
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-            if (!div_fast_ok(v[k])) q[k] = __fdiv_rn(v[k], b);
-    }
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = q[k];
 }
 
 // 4-byte copy to shared address sa + OFF (n = 4: copy, n = 0: zero-fill)
@@ -284,11 +258,10 @@ __device__ __forceinline__ void fir_ring_body(int pass, const GridRef* __restric
                 const float nrm = norm[y];
                 const float rcp = rnorm[y];
                 float* orow = out + (long long)y * out_row;
-                float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
-                div_rn_warp<4>(v, nrm, rcp);  // y < R is the same for the whole warp
+                const float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (ok[k]) orow[ooff[k]] = v[k];
+                    if (ok[k]) orow[ooff[k]] = div_rn(v[k], nrm, rcp);
             }
         }
     }
