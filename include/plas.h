@@ -504,7 +504,7 @@ int plas_batch_sort(int n, const plas_job* jobs, int D, const float* weights,
  *   PLAS_ERR_INVALID_ARG for unsupported sizes.
  * plas_set_tuning: installs *t for (H, W, D) on the current device
  *   (t == NULL removes the entry); plas_get_tuning: what a sort of this
- *   shape on the current device would use (the defaults 8, 96 and 4 when
+ *   shape on the current device would use (the defaults 12, 96 and 4 when
  *   nothing is installed).  A radius r takes the small-radius path when
  *   r < fir_small_below (both passes in one launch when small_fused is 1,
  *   r <= 11 and D <= 16; otherwise the direct kernel), else the 64-row one
@@ -530,7 +530,8 @@ typedef struct plas_tuning {
     int large_tma;          /* 1: the large tiling streams its input rows with */
                             /* tensor copies (persistent CTAs, single grids of */
                             /* an even D with an instantiated row box); 0: the */
-                            /* chunked ring.  Default 1                        */
+                            /* chunked ring.  Default 0 (the chunked ring was  */
+                            /* faster on every grid measured)                  */
     float fir_large_ring_us[PLAS_TUNE_MAX_RADII]; /* both passes, chunked    */
     float fir_large_tma_us[PLAS_TUNE_MAX_RADII];  /* both passes, tensor      */
                                                   /* copies; -1: not eligible */

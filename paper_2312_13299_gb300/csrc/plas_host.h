@@ -88,14 +88,15 @@ size_t sort_workspace_bytes(int H, int W, int D, const plas_schedule& s);
 // for (D, H, W), else the entry with the same D and the nearest cell count,
 // else the defaults.
 constexpr int kDirectTuneMaxR = 32;  // the tuner times the direct FIR kernel up to this radius
-constexpr int kDefaultSmallBelow = 8;
+constexpr int kDefaultSmallBelow = 12;
 constexpr int kDefaultMediumBelow = 96;
 constexpr int kDefaultAssignPerSm = 4;
 struct Tuning {
-    int small_below = kDefaultSmallBelow;    // direct FIR kernel (no ring) below this radius
+    int small_below = kDefaultSmallBelow;    // small-radius path (one launch, or direct) below this radius
     int medium_below = kDefaultMediumBelow;  // else 64-row below this one, else 128-row
     int assign_per_sm = kDefaultAssignPerSm;
-    int large_tma = 1;  // the large tiling streams rows with tensor copies where a grid allows
+    int large_tma = 0;  // 1: the large tiling streams rows with tensor copies where a grid allows
+                        // (measured slower than the ring everywhere; the tuner may pick it)
     int small_fused = 1;  // small radii run both passes in one launch where eligible
 };
 inline int fir_tiling(int r, const Tuning& t) {

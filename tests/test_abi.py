@@ -44,7 +44,7 @@ def test_library_is_sm103a_only():
 
 
 # (fir_small_below, fir_medium_below, assign_ctas_per_sm) when nothing is installed
-DEFAULT_TUNING = (8, 96, 4)
+DEFAULT_TUNING = (12, 96, 4)
 
 
 def test_tuning_table_round_trip_host_only():
